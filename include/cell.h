@@ -1,0 +1,198 @@
+/*
+ * cell.h -- C ABI of the GB300 periodic piezoelectric unit-cell library.
+ *
+ * The library solves the nine periodic cell problems of linear piezoelectric
+ * homogenisation (Wegert, Roberts & Challis, arXiv 2410.03148, §2.2) on a
+ * structured grid of Q1 hexahedra with 4 dofs per node (u1, u2, u3, phi) and
+ * a per-element ersatz scale rho_e (§2.6), by approximate-Schur-complement
+ * preconditioned GMRES (§2.5.3), and reduces the solutions to the homogenised
+ * tensors C^H, e^H, kappa^H (Eqs. hom_C, hom_e, hom_kappa) and to element-wise
+ * sensitivities.  All device work runs in the library's own sm_103a kernels on
+ * the caller's CUDA stream.
+ *
+ * Conventions used throughout
+ * ---------------------------
+ * Grid.  The unit cell [0,1)^3 is split into nx*ny*nz boxes; nodes are
+ *   periodic, so there are nx*ny*nz nodes and nx*ny*nz elements.  Node and
+ *   element (i,j,k) both have flat index i + nx*(j + ny*k) (x fastest).
+ *   Element (i,j,k) spans nodes (i+a, j+b, k+c) mod (nx,ny,nz), a,b,c in {0,1}.
+ * Tensors.  IEEE Voigt order (11,22,33,23,13,12), row-major, SI units:
+ *   C[6x6] in Pa, e[3x6] in C/m^2, kappa[3x3] in F/m.  Engineering shear.
+ * Loads.  Load I = 0..5 is the unit macroscopic strain of Voigt component I,
+ *   I = 6..8 the unit macroscopic electric field along x, y, z (§2.2).
+ * Field vectors on device ("cell vectors").  A set of nrhs nodal fields is
+ *   stored component-planar: value(load r, component c, node n) at offset
+ *   (r*4 + c)*N + n with N = nx*ny*nz, c in {u1,u2,u3,phi}.
+ * Units inside.  The system is solved in the nondimensional variables of
+ *   §2.2 (C/C0, e/sqrt(C0 k0), kappa/k0 with C0 = max|C|, k0 = max|kappa|);
+ *   vectors exchanged through cell_apply / cell_rhs / cell_get_solution are
+ *   in those units.  Homogenised tensors are returned in SI units.
+ * Ownership.  The caller owns every pointer it passes.  cell_setup copies
+ *   the design (rho or phi) into library-owned device memory, so the caller's
+ *   buffer may be freed or reused after it returns.  The library owns its
+ *   workspaces (allocated in cell_setup, freed in cell_destroy).
+ * Streams.  Every call enqueues its device work on the stream given in the
+ *   descriptor (0 = legacy default stream).  Calls that return host results
+ *   (cell_solve's stats, cell_homogenise) synchronise that stream.
+ * Errors.  Every int-returning call returns a cell_status.  Invalid sizes,
+ *   null pointers and unknown enums give CELL_EINVAL without touching the
+ *   device.  CUDA failures give CELL_ECUDA; cell_last_error() describes the
+ *   most recent failure of the calling thread.
+ */
+#ifndef PIEZO_CELL_H
+#define PIEZO_CELL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cell_status {
+  CELL_OK = 0,
+  CELL_EINVAL = 1,     /* invalid argument; nothing was done */
+  CELL_ENOMEM = 2,     /* device allocation failed */
+  CELL_ENOTCONV = 3,   /* solver stopped before reaching tol; stats filled */
+  CELL_ETIMEOUT = 4,   /* a bounded device wait expired */
+  CELL_ECUDA = 5,      /* a CUDA runtime call failed (see cell_last_error) */
+  CELL_ESTATE = 6      /* call out of order (e.g. homogenise before solve) */
+} cell_status;
+
+typedef enum cell_precision {
+  CELL_FP64 = 0,        /* every operator, smoother and Krylov vector in FP64 */
+  CELL_MIXED_FP32 = 1   /* FP32 GMRES + multigrid inside FP64 iterative refinement */
+} cell_precision;
+
+typedef enum cell_input_kind {
+  CELL_INPUT_RHO = 0,   /* input = per-element ersatz scale rho_e > 0 */
+  CELL_INPUT_PHI = 1    /* input = nodal level-set values; rho from §2.6 smoothing */
+} cell_input_kind;
+
+typedef enum cell_dtype { CELL_F32 = 0, CELL_F64 = 1 } cell_dtype;
+
+typedef struct cell_options {
+  double tol;          /* stop when ||r_I||_2 <= tol * ||b_I||_2 for every load I
+                          (true residual of the nondimensional system, FP64) */
+  int restart;         /* GMRES restart length m (1..64) */
+  int max_iter;        /* cap on GMRES iterations per load over the whole solve */
+  int precision;       /* cell_precision */
+  double inner_tol;    /* MIXED: relative residual reduction asked of each FP32
+                          GMRES solve inside the FP64 refinement loop */
+  int max_refine;      /* MIXED: cap on FP64 refinement steps */
+  int vcycles_u;       /* V-cycles approximating A^-1 (elastic block) per application */
+  int vcycles_phi;     /* V-cycles approximating Sbar^-1 (Schur block) per application */
+  int cheb_degree;     /* Chebyshev-Jacobi smoothing steps per pre/post smoothing */
+  double cheb_lo;      /* lower end of the Chebyshev interval, as a fraction of
+                          the upper end */
+  double cheb_hi;      /* multiplier applied to the element-wise lambda_max bound */
+  double schur_shift;  /* diagonal shift added to A_e before inverting it in
+                          Sbar = sum_e C_e + B_e A_e^-1 B_e^T (§2.5.3, 1e-10) */
+  int coarse_dofs;     /* stop coarsening once a level has at most this many dofs */
+  int load_mask;       /* bit I set = solve load I (default 0x1FF = all nine) */
+  int profile;         /* nonzero: time the operator-apply kernels with CUDA events */
+} cell_options;
+
+typedef struct cell_desc {
+  int nx, ny, nz;      /* elements (= periodic nodes) per direction, each >= 2 */
+  double C[36];        /* base stiffness, Pa */
+  double e[18];        /* base piezoelectric coupling, C/m^2 */
+  double kappa[9];     /* base permittivity, F/m */
+  int input_kind;      /* cell_input_kind */
+  int input_dtype;     /* cell_dtype of *input */
+  const void* input;   /* DEVICE pointer, nx*ny*nz values, x fastest */
+  double rho_void;     /* PHI input: void scale (paper: small ersatz value, default 1e-3) */
+  double eta;          /* PHI input: smoothing half-width in phi units; <= 0 selects
+                          2*max(1/nx,1/ny,1/nz) ("within two elements", §2.6) */
+  cell_options opt;
+  void* stream;        /* cudaStream_t */
+} cell_desc;
+
+typedef struct cell_stats {
+  int status;               /* cell_status of the solve */
+  int iters[9];             /* GMRES iterations per load (all refinement steps) */
+  int refinements;          /* FP64 refinement steps taken (MIXED) */
+  int nlevels_u, nlevels_phi;
+  double rel_residual[9];   /* final true relative residual per load (FP64) */
+  double solve_ms;          /* host wall time of cell_solve */
+  double apply_ms;          /* profile: summed device time of full-operator applies */
+  int apply_count;          /* profile: number of full-operator applies timed */
+  double smooth_ms;         /* profile: summed device time of block-operator applies */
+  int smooth_count;
+} cell_stats;
+
+typedef struct cell_handle cell_handle;
+
+/* Fill *opt with the defaults (tol 1e-10, restart 30, MIXED_FP32, ...). */
+void cell_default_options(cell_options* opt);
+
+/* Build everything that depends only on the design (S1 of the hot path):
+ * nondimensionalise the material, form the 32x32 element matrix K0 by 2x2x2
+ * Gauss integration and the 8x8 local Schur complement S0 (§2.5.3), map the
+ * design to rho_e on the device (smoothed Heaviside of the element-mean level
+ * set for PHI input), and build the multigrid hierarchies of both
+ * preconditioner blocks (Galerkin coarse element matrices, Jacobi diagonals,
+ * Chebyshev bounds, coarsest dense inverse).  On success *out receives a new
+ * handle.  Errors: CELL_EINVAL for sizes < 2, NaN/non-positive tolerances,
+ * unknown enums or null pointers; CELL_ENOMEM; CELL_ECUDA. */
+int cell_setup(const cell_desc* d, cell_handle** out);
+
+/* Solve the selected cell problems (§2.2) for the design of the handle:
+ * assemble b = -sum_e rho_e P_e^T K0 Zbar_e (negated potential rows, the
+ * nonsymmetric form of Eq. (sym-piezo)), run right-preconditioned SCP-GMRES
+ * (§2.5.3), and project the null space (mean displacement and potential) out
+ * of the solutions.  st may be NULL.  Returns CELL_ENOTCONV (with stats and a
+ * usable best solution) if tol was not reached within max_iter/max_refine. */
+int cell_solve(cell_handle* h, cell_stats* st);
+
+/* Homogenised tensors of the last solve (Eqs. hom_C, hom_e, hom_kappa with
+ * Vol(D) = 1), in SI units, written to host arrays CH[36], eH[18], kH[9].
+ * Computed in FP64 in the energy form H_IJ = sum_e rho_e W_e^I.K0 W_e^J
+ * (W = total nodal field), whose error is quadratic in the solve error.
+ * Needs all nine loads; CELL_ESTATE before a successful solve. */
+int cell_homogenise(cell_handle* h, double CH[36], double eH[18], double kH[9]);
+
+/* Element-wise sensitivities of L = sum dC.C^H + de.e^H + dk.kappa^H with
+ * respect to rho_e (the adjoint states are the cell solutions themselves, as
+ * the energy form is stationary in the fluctuations).  dC[36], de[18], dk[9]
+ * are host arrays (any may be NULL = zero).  g is a DEVICE array of nx*ny*nz
+ * values of dtype (CELL_F32 or CELL_F64), element-indexed.  The per-element
+ * quadratic forms are evaluated in the dtype given.  CELL_ESTATE before a
+ * successful solve. */
+int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18],
+                     const double dk[9], void* g, int dtype);
+
+/* Hydrostatic strain coefficient d_h = d31 + d32 + d33 with d = e S, S = C^-1
+ * (§2.3), and its gradient with respect to every entry of C (dC[36]) and
+ * e (de[18]).  Host-only helper; dC/de may be NULL.  CELL_EINVAL if C is
+ * singular. */
+int cell_dh(const double C[36], const double e[18], double* dh, double dC[36], double de[18]);
+
+/* Copy the solutions (total fluctuation fields, loads in order 0..8 whether or
+ * not solved) as FP64 cell vectors into the DEVICE buffer out (9*4*N values). */
+int cell_get_solution(cell_handle* h, double* out);
+
+/* y = Ahat x for nrhs cell vectors (device pointers, dtype CELL_F32 or
+ * CELL_F64): the assembled nonsymmetric operator of Eq. (sym-piezo) second
+ * form, sum_e rho_e P_e^T K0 P_e x with the potential rows negated. */
+int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype);
+
+/* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as
+ * FP64 cell vectors into the DEVICE buffer out (9*4*N values). */
+int cell_rhs(cell_handle* h, double* out);
+
+/* The per-element scale rho_e the handle uses, FP64, into DEVICE out (N values). */
+int cell_get_rho(cell_handle* h, double* out);
+
+/* Host: the nondimensional 32x32 element matrix K0 (row-major, local dof
+ * 4*n + c, local node n = a + 2b + 4c at corner (a,b,c)) and the 8x8 local
+ * Schur complement S0 for the material and grid of d (d->input unused). */
+int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]);
+
+void cell_destroy(cell_handle* h);
+const char* cell_status_str(int status);
+const char* cell_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PIEZO_CELL_H */

@@ -1,0 +1,230 @@
+"""ctypes binding of ``libcell.so`` (include/cell.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls.  Device
+buffers are passed as torch CUDA tensors (their ``data_ptr()``), streams as
+torch streams; PyTorch provides memory and streams, all computation runs in
+the library's CUDA kernels.  The library must have been built
+(``paper_2410_03148_gb300.build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcell.so")
+
+CELL_OK, CELL_EINVAL, CELL_ENOMEM, CELL_ENOTCONV, CELL_ETIMEOUT, CELL_ECUDA, CELL_ESTATE = range(7)
+CELL_FP64, CELL_MIXED_FP32 = 0, 1
+CELL_INPUT_RHO, CELL_INPUT_PHI = 0, 1
+CELL_F32, CELL_F64 = 0, 1
+
+# every symbol include/cell.h declares
+EXPORTS = [
+    "cell_default_options", "cell_setup", "cell_solve", "cell_homogenise", "cell_sensitivity",
+    "cell_dh", "cell_get_solution", "cell_apply", "cell_rhs", "cell_get_rho",
+    "cell_element_matrices", "cell_destroy", "cell_status_str", "cell_last_error",
+]
+
+
+class cell_options(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("restart", C.c_int), ("max_iter", C.c_int), ("precision", C.c_int),
+        ("inner_tol", C.c_double), ("max_refine", C.c_int), ("vcycles_u", C.c_int),
+        ("vcycles_phi", C.c_int), ("cheb_degree", C.c_int), ("cheb_lo", C.c_double),
+        ("cheb_hi", C.c_double), ("schur_shift", C.c_double), ("coarse_dofs", C.c_int),
+        ("load_mask", C.c_int), ("profile", C.c_int),
+    ]
+
+
+class cell_desc(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("C", C.c_double * 36), ("e", C.c_double * 18), ("kappa", C.c_double * 9),
+        ("input_kind", C.c_int), ("input_dtype", C.c_int), ("input", C.c_void_p),
+        ("rho_void", C.c_double), ("eta", C.c_double), ("opt", cell_options),
+        ("stream", C.c_void_p),
+    ]
+
+
+class cell_stats(C.Structure):
+    _fields_ = [
+        ("status", C.c_int), ("iters", C.c_int * 9), ("refinements", C.c_int),
+        ("nlevels_u", C.c_int), ("nlevels_phi", C.c_int), ("rel_residual", C.c_double * 9),
+        ("solve_ms", C.c_double), ("apply_ms", C.c_double), ("apply_count", C.c_int),
+        ("smooth_ms", C.c_double), ("smooth_count", C.c_int),
+    ]
+
+
+class CellError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        super().__init__(f"{fn} failed: {_str(status)} ({status}); {_last()}")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcell.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    D = C.POINTER(C.c_double)
+    lib.cell_default_options.argtypes = [C.POINTER(cell_options)]
+    lib.cell_default_options.restype = None
+    lib.cell_setup.argtypes = [C.POINTER(cell_desc), C.POINTER(P)]
+    lib.cell_solve.argtypes = [P, C.POINTER(cell_stats)]
+    lib.cell_homogenise.argtypes = [P, D, D, D]
+    lib.cell_sensitivity.argtypes = [P, D, D, D, P, C.c_int]
+    lib.cell_dh.argtypes = [D, D, D, D, D]
+    lib.cell_get_solution.argtypes = [P, P]
+    lib.cell_apply.argtypes = [P, P, P, C.c_int, C.c_int]
+    lib.cell_rhs.argtypes = [P, P]
+    lib.cell_get_rho.argtypes = [P, P]
+    lib.cell_element_matrices.argtypes = [C.POINTER(cell_desc), D, D]
+    lib.cell_destroy.argtypes = [P]
+    lib.cell_destroy.restype = None
+    lib.cell_status_str.argtypes = [C.c_int]
+    lib.cell_status_str.restype = C.c_char_p
+    lib.cell_last_error.argtypes = []
+    lib.cell_last_error.restype = C.c_char_p
+    for name in ("cell_setup", "cell_solve", "cell_homogenise", "cell_sensitivity", "cell_dh",
+                 "cell_get_solution", "cell_apply", "cell_rhs", "cell_get_rho",
+                 "cell_element_matrices"):
+        getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _str(s):
+    return load().cell_status_str(s).decode()
+
+
+def _last():
+    return load().cell_last_error().decode()
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(fn, s, ok=(CELL_OK,)):
+    if s not in ok:
+        raise CellError(fn, s)
+    return s
+
+
+def cell_status_str(s: int) -> str:
+    return _str(s)
+
+
+def cell_last_error() -> str:
+    return _last()
+
+
+def cell_default_options(**overrides) -> cell_options:
+    o = cell_options()
+    load().cell_default_options(C.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def make_desc(shape_xyz, C6, e36, kappa3, input_ptr, input_kind, input_dtype, opt=None,
+              stream=0, rho_void=1e-3, eta=0.0) -> cell_desc:
+    d = cell_desc()
+    d.nx, d.ny, d.nz = (int(v) for v in shape_xyz)
+    d.C[:] = np.asarray(C6, dtype=np.float64).ravel().tolist()
+    d.e[:] = np.asarray(e36, dtype=np.float64).ravel().tolist()
+    d.kappa[:] = np.asarray(kappa3, dtype=np.float64).ravel().tolist()
+    d.input_kind = input_kind
+    d.input_dtype = input_dtype
+    d.input = C.c_void_p(input_ptr)
+    d.rho_void = rho_void
+    d.eta = eta
+    d.opt = opt if opt is not None else cell_default_options()
+    d.stream = C.c_void_p(stream)
+    return d
+
+
+def cell_setup(desc: cell_desc):
+    h = C.c_void_p()
+    _check("cell_setup", load().cell_setup(C.byref(desc), C.byref(h)))
+    return h
+
+
+def cell_solve(h, allow_notconv=False):
+    st = cell_stats()
+    s = load().cell_solve(h, C.byref(st))
+    _check("cell_solve", s, (CELL_OK, CELL_ENOTCONV) if allow_notconv else (CELL_OK,))
+    return s, st
+
+
+def cell_homogenise(h):
+    CH, eH, kH = np.zeros(36), np.zeros(18), np.zeros(9)
+    lib = load()
+    s = lib.cell_homogenise(h, CH.ctypes.data_as(C.POINTER(C.c_double)),
+                            eH.ctypes.data_as(C.POINTER(C.c_double)),
+                            kH.ctypes.data_as(C.POINTER(C.c_double)))
+    _check("cell_homogenise", s)
+    return CH.reshape(6, 6), eH.reshape(3, 6), kH.reshape(3, 3)
+
+
+def cell_sensitivity(h, dC, de, dk, g_ptr: int, dtype: int):
+    keep = []
+    args = []
+    for a, n in ((dC, 36), (de, 18), (dk, 9)):
+        if a is None:
+            args.append(None)
+        else:
+            arr, p = _dptr(np.asarray(a).reshape(n))
+            keep.append(arr)
+            args.append(p)
+    _check("cell_sensitivity", load().cell_sensitivity(h, *args, C.c_void_p(g_ptr), dtype))
+
+
+def cell_dh(Cm, em):
+    Ca, Cp = _dptr(np.asarray(Cm).reshape(36))
+    ea, ep = _dptr(np.asarray(em).reshape(18))
+    dh = C.c_double()
+    dC, de = np.zeros(36), np.zeros(18)
+    _check("cell_dh", load().cell_dh(Cp, ep, C.byref(dh), dC.ctypes.data_as(C.POINTER(C.c_double)),
+                                       de.ctypes.data_as(C.POINTER(C.c_double))))
+    return dh.value, dC.reshape(6, 6), de.reshape(3, 6)
+
+
+def cell_get_solution(h, out_ptr: int):
+    _check("cell_get_solution", load().cell_get_solution(h, C.c_void_p(out_ptr)))
+
+
+def cell_apply(h, x_ptr: int, y_ptr: int, nrhs: int, dtype: int):
+    _check("cell_apply", load().cell_apply(h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nrhs, dtype))
+
+
+def cell_rhs(h, out_ptr: int):
+    _check("cell_rhs", load().cell_rhs(h, C.c_void_p(out_ptr)))
+
+
+def cell_get_rho(h, out_ptr: int):
+    _check("cell_get_rho", load().cell_get_rho(h, C.c_void_p(out_ptr)))
+
+
+def cell_element_matrices(desc: cell_desc):
+    K0, S0 = np.zeros(1024), np.zeros(64)
+    _check("cell_element_matrices", load().cell_element_matrices(
+        C.byref(desc), K0.ctypes.data_as(C.POINTER(C.c_double)),
+        S0.ctypes.data_as(C.POINTER(C.c_double))))
+    return K0.reshape(32, 32), S0.reshape(8, 8)
+
+
+def cell_destroy(h):
+    load().cell_destroy(h)

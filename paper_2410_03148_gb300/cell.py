@@ -1,0 +1,111 @@
+"""Pythonic handle over the C ABI (argument marshalling only).
+
+``Cell`` owns one ``cell_handle``: a periodic unit-cell design (per-element
+ersatz scale rho or nodal level set phi, a CUDA tensor of shape (nz, ny, nx))
+with its material, and exposes the library calls on torch tensors.  All work
+runs in libcell.so's kernels on the current torch CUDA stream.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _binding as B
+
+
+def _stream_ptr(device):
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Cell:
+    def __init__(self, design: torch.Tensor, material, kind: str = "phi", rho_void: float = 1e-3,
+                 eta: float = 0.0, **options):
+        if not design.is_cuda:
+            raise ValueError("design must be a CUDA tensor (the library has no CPU path)")
+        if design.dim() != 3:
+            raise ValueError("design must have shape (nz, ny, nx)")
+        if design.dtype not in (torch.float32, torch.float64):
+            raise ValueError("design dtype must be float32 or float64")
+        B.load()
+        self.device = design.device
+        self.shape = tuple(design.shape)
+        nz, ny, nx = self.shape
+        design = design.contiguous()
+        Cm, em, km = material
+        opt = B.cell_default_options(**options)
+        kind_id = B.CELL_INPUT_PHI if kind == "phi" else B.CELL_INPUT_RHO
+        dt = B.CELL_F32 if design.dtype == torch.float32 else B.CELL_F64
+        with torch.cuda.device(self.device):
+            self._desc = B.make_desc((nx, ny, nz), Cm, em, km, design.data_ptr(), kind_id, dt, opt,
+                                     _stream_ptr(self.device), rho_void, eta)
+            self._h = B.cell_setup(self._desc)
+        self.nn = nx * ny * nz
+        self.stats = None
+
+    # -- hot path --------------------------------------------------------------
+    def solve(self, allow_notconv: bool = False):
+        status, st = B.cell_solve(self._h, allow_notconv)
+        self.stats = {
+            "status": status,
+            "iters": list(st.iters),
+            "refinements": st.refinements,
+            "rel_residual": list(st.rel_residual),
+            "solve_ms": st.solve_ms,
+            "apply_ms": st.apply_ms,
+            "apply_count": st.apply_count,
+            "smooth_ms": st.smooth_ms,
+            "smooth_count": st.smooth_count,
+            "nlevels_u": st.nlevels_u,
+            "nlevels_phi": st.nlevels_phi,
+        }
+        return self.stats
+
+    def homogenise(self):
+        """(C^H [6x6] Pa, e^H [3x6] C/m^2, kappa^H [3x3] F/m) as numpy FP64."""
+        return B.cell_homogenise(self._h)
+
+    def sensitivity(self, dC=None, de=None, dk=None, dtype=torch.float64) -> torch.Tensor:
+        g = torch.empty(self.shape, dtype=dtype, device=self.device)
+        B.cell_sensitivity(self._h, dC, de, dk, g.data_ptr(),
+                           B.CELL_F32 if dtype == torch.float32 else B.CELL_F64)
+        return g
+
+    # -- parity / inspection -----------------------------------------------------
+    def apply(self, x: torch.Tensor) -> torch.Tensor:
+        """y = Ahat x for x of shape (nrhs, 4, nz, ny, nx) (float32 or float64)."""
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        B.cell_apply(self._h, x.data_ptr(), y.data_ptr(), x.shape[0],
+                     B.CELL_F32 if x.dtype == torch.float32 else B.CELL_F64)
+        return y
+
+    def rhs(self) -> torch.Tensor:
+        out = torch.empty((9, 4) + self.shape, dtype=torch.float64, device=self.device)
+        B.cell_rhs(self._h, out.data_ptr())
+        return out
+
+    def solution(self) -> torch.Tensor:
+        out = torch.empty((9, 4) + self.shape, dtype=torch.float64, device=self.device)
+        B.cell_get_solution(self._h, out.data_ptr())
+        return out
+
+    def rho(self) -> torch.Tensor:
+        out = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        B.cell_get_rho(self._h, out.data_ptr())
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            B.cell_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dh(C, e):
+    """d_h and its gradients (host helper of the library)."""
+    return B.cell_dh(C, e)

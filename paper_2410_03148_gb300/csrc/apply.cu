@@ -1,0 +1,276 @@
+// Matrix-free operator applies on the periodic Q1 grid (the hot loop of the
+// solver): y = sum_e w_e P_e^T K P_e x, node-centric.
+//
+// Each thread owns one (node, load) pair and computes the rows of its node
+// from the 8 elements around it, gathering the 27 neighbouring nodes once.
+// No thread writes another node's value, so there are no atomics and results
+// are bitwise reproducible.  For fixed-matrix operators (level 0: w_e = rho_e,
+// K = a block of the 32x32 element matrix K0 or the 8x8 local Schur matrix S0)
+// the matrix is a by-value kernel parameter, so every multiply-add reads its
+// coefficient straight from the constant bank.  Coarse multigrid levels carry
+// one Galerkin matrix per element, stored entry-major (coalesced).
+//
+// Operator definitions: Eq. (sym-piezo) and its nonsymmetric second form
+// (potential rows negated), §2.5; block operators of P_SCP, §2.5.3.
+#include "kernels.cuh"
+
+namespace cell {
+
+namespace {
+
+constexpr int kBlock = 128;
+
+struct NodeIdx {
+  i64 xo[3], yo[3], zo[3];
+  i64 n, nn;
+};
+
+__device__ __forceinline__ bool node_index(int nx, int ny, int nz, NodeIdx& t) {
+  const i64 nxy = (i64)nx * ny;
+  t.nn = nxy * nz;
+  t.n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t.n >= t.nn) return false;
+  const int i = (int)(t.n % nx);
+  const i64 q = t.n / nx;
+  const int j = (int)(q % ny);
+  const int k = (int)(q / ny);
+  t.xo[0] = i == 0 ? nx - 1 : i - 1;
+  t.xo[1] = i;
+  t.xo[2] = i == nx - 1 ? 0 : i + 1;
+  t.yo[0] = (i64)(j == 0 ? ny - 1 : j - 1) * nx;
+  t.yo[1] = (i64)j * nx;
+  t.yo[2] = (i64)(j == ny - 1 ? 0 : j + 1) * nx;
+  t.zo[0] = (i64)(k == 0 ? nz - 1 : k - 1) * nxy;
+  t.zo[1] = (i64)k * nxy;
+  t.zo[2] = (i64)(k == nz - 1 ? 0 : k + 1) * nxy;
+  return true;
+}
+
+// Store the NCO output components of one node according to MODE.
+// acc = (A x)_node, dold = this node's own gathered input (CHEB modes).
+template <typename T, int NCO, int MODE>
+__device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const NodeIdx& t,
+                                         const T* acc, const T* dold) {
+#pragma unroll
+  for (int c = 0; c < NCO; ++c) {
+    const i64 o = (i64)c * t.nn + t.n;
+    if (MODE == AM_LINEAR) {
+      T v = a.alpha * acc[c];
+      if (a.b) v += a.beta * a.b[r * a.bs + o];
+      a.y[r * a.ys + o] = v;
+    } else if (MODE == AM_CHEB || MODE == AM_CHEB_LAST) {
+      const T rr = a.y[r * a.ys + o] - acc[c];
+      a.y[r * a.ys + o] = rr;
+      T* sp = a.sol + r * a.ss + o;
+      *sp = (a.sol_zero ? T(0) : *sp) + dold[c];
+      if (MODE == AM_CHEB) a.dout[r * a.ds + o] = a.c1 * dold[c] + a.c2 * a.dinv[o] * rr;
+    } else {  // AM_RESID_CHEB0
+      const T rr = a.b[r * a.bs + o] - acc[c];
+      a.y[r * a.ys + o] = rr;
+      a.dout[r * a.ds + o] = a.c2 * a.dinv[o] * rr;
+    }
+  }
+}
+
+// Fixed-matrix operator, FP32: the 27 neighbours are preloaded into registers
+// and every coefficient index is a compile-time constant.
+template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
+  const int r = blockIdx.y;
+  if (a.active && !a.active[r]) return;
+  NodeIdx t;
+  if (!node_index(a.nx, a.ny, a.nz, t)) return;
+  const T* X = a.x + r * a.xs;
+  T xs[27][NCI];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const i64 m = t.xo[q % 3] + t.yo[(q / 3) % 3] + t.zo[q / 9];
+#pragma unroll
+    for (int d = 0; d < NCI; ++d) xs[q][d] = __ldg(X + d * t.nn + m);
+  }
+  T acc[NCO];
+#pragma unroll
+  for (int c = 0; c < NCO; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+    const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+    const T w = __ldg(a.rho + t.xo[ex] + t.yo[ey] + t.zo[ez]);
+    T tl[NCO];
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) tl[c] = T(0);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int q = (ex + (b & 1)) + 3 * (ey + ((b >> 1) & 1)) + 9 * (ez + (b >> 2));
+#pragma unroll
+      for (int c = 0; c < NCO; ++c)
+#pragma unroll
+        for (int d = 0; d < NCI; ++d)
+          tl[c] = fma(M.k[(la * NCM + R0 + c) * (8 * NCM) + b * NCM + C0 + d], xs[q][d], tl[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) acc[c] = fma(w, tl[c], acc[c]);
+  }
+  if (NEGLAST) acc[NCO - 1] = -acc[NCO - 1];
+  T dold[NCO];
+#pragma unroll
+  for (int c = 0; c < NCO; ++c) dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? xs[13][c] : T(0);
+  epilogue<T, NCO, MODE>(a, r, t, acc, dold);
+}
+
+// Fixed-matrix operator, FP64: neighbours are loaded per element (FP64
+// arithmetic, not load bandwidth, bounds this variant on GB300).
+template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_apply_fixed_ld(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
+  const int r = blockIdx.y;
+  if (a.active && !a.active[r]) return;
+  NodeIdx t;
+  if (!node_index(a.nx, a.ny, a.nz, t)) return;
+  const T* X = a.x + r * a.xs;
+  T acc[NCO];
+#pragma unroll
+  for (int c = 0; c < NCO; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+    const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+    const T w = __ldg(a.rho + t.xo[ex] + t.yo[ey] + t.zo[ez]);
+    T tl[NCO];
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) tl[c] = T(0);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const i64 m = t.xo[ex + (b & 1)] + t.yo[ey + ((b >> 1) & 1)] + t.zo[ez + (b >> 2)];
+#pragma unroll
+      for (int d = 0; d < NCI; ++d) {
+        const T xv = __ldg(X + d * t.nn + m);
+#pragma unroll
+        for (int c = 0; c < NCO; ++c)
+          tl[c] = fma(M.k[(la * NCM + R0 + c) * (8 * NCM) + b * NCM + C0 + d], xv, tl[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) acc[c] = fma(w, tl[c], acc[c]);
+  }
+  if (NEGLAST) acc[NCO - 1] = -acc[NCO - 1];
+  T dold[NCO];
+#pragma unroll
+  for (int c = 0; c < NCO; ++c)
+    dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? X[c * t.nn + t.n] : T(0);
+  epilogue<T, NCO, MODE>(a, r, t, acc, dold);
+}
+
+// Per-element (Galerkin) matrices on a coarse level.
+template <typename T, int NC, int MODE>
+__global__ void __launch_bounds__(kBlock) k_apply_elem(const ApplyArgs<T> a) {
+  const int r = blockIdx.y;
+  if (a.active && !a.active[r]) return;
+  NodeIdx t;
+  if (!node_index(a.nx, a.ny, a.nz, t)) return;
+  const T* X = a.x + r * a.xs;
+  const i64 ne = t.nn;
+  T acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+    const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+    const i64 el = t.xo[ex] + t.yo[ey] + t.zo[ez];
+    const T* K = a.ke + (i64)(la * NC) * (8 * NC) * ne + el;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const i64 m = t.xo[ex + (b & 1)] + t.yo[ey + ((b >> 1) & 1)] + t.zo[ez + (b >> 2)];
+#pragma unroll
+      for (int d = 0; d < NC; ++d) {
+        const T xv = __ldg(X + d * t.nn + m);
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          acc[c] = fma(__ldg(K + (i64)(c * 8 * NC + b * NC + d) * ne), xv, acc[c]);
+      }
+    }
+  }
+  T dold[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? X[c * t.nn + t.n] : T(0);
+  epilogue<T, NC, MODE>(a, r, t, acc, dold);
+}
+
+inline dim3 grid_for(const ApplyArgs<float>& a, int nrhs) {
+  const i64 nn = (i64)a.nx * a.ny * a.nz;
+  return dim3((unsigned)((nn + kBlock - 1) / kBlock), (unsigned)nrhs);
+}
+inline dim3 grid_for(const ApplyArgs<double>& a, int nrhs) {
+  const i64 nn = (i64)a.nx * a.ny * a.nz;
+  return dim3((unsigned)((nn + kBlock - 1) / kBlock), (unsigned)nrhs);
+}
+
+template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEG, int MODE>
+void launch_fixed(const ApplyArgs<T>& a, const FixedMat<T, NCM>& M, int nrhs, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4)
+    k_apply_fixed_pre<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
+  else
+    k_apply_fixed_ld<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
+}
+
+template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEG>
+void dispatch_fixed(const ApplyArgs<T>& a, const FixedMat<T, NCM>& M, int mode, int nrhs,
+                    cudaStream_t s) {
+  switch (mode) {
+    case AM_LINEAR: launch_fixed<T, NCM, NCI, NCO, R0, C0, NEG, AM_LINEAR>(a, M, nrhs, s); break;
+    case AM_CHEB: launch_fixed<T, NCM, NCI, NCO, R0, C0, NEG, AM_CHEB>(a, M, nrhs, s); break;
+    case AM_CHEB_LAST: launch_fixed<T, NCM, NCI, NCO, R0, C0, NEG, AM_CHEB_LAST>(a, M, nrhs, s); break;
+    default: launch_fixed<T, NCM, NCI, NCO, R0, C0, NEG, AM_RESID_CHEB0>(a, M, nrhs, s); break;
+  }
+}
+
+}  // namespace
+
+template <typename T>
+void apply_full(const ApplyArgs<T>& a, const FixedMat<T, 4>& M, int mode, int nrhs, cudaStream_t s) {
+  // only LINEAR is meaningful for the full (nonsymmetric) operator
+  (void)mode;
+  launch_fixed<T, 4, 4, 4, 0, 0, true, AM_LINEAR>(a, M, nrhs, s);
+}
+
+template <typename T>
+void apply_uu(const ApplyArgs<T>& a, const FixedMat<T, 4>& M, int mode, int nrhs, cudaStream_t s) {
+  dispatch_fixed<T, 4, 3, 3, 0, 0, false>(a, M, mode, nrhs, s);
+}
+
+template <typename T>
+void apply_pu(const ApplyArgs<T>& a, const FixedMat<T, 4>& M, int nrhs, cudaStream_t s) {
+  launch_fixed<T, 4, 3, 1, 3, 0, false, AM_LINEAR>(a, M, nrhs, s);
+}
+
+template <typename T>
+void apply_ss(const ApplyArgs<T>& a, const FixedMat<T, 1>& M, int mode, int nrhs, cudaStream_t s) {
+  dispatch_fixed<T, 1, 1, 1, 0, 0, false>(a, M, mode, nrhs, s);
+}
+
+template <typename T, int NC>
+void apply_elem(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
+  const dim3 g = grid_for(a, nrhs);
+  switch (mode) {
+    case AM_LINEAR: k_apply_elem<T, NC, AM_LINEAR><<<g, kBlock, 0, s>>>(a); break;
+    case AM_CHEB: k_apply_elem<T, NC, AM_CHEB><<<g, kBlock, 0, s>>>(a); break;
+    case AM_CHEB_LAST: k_apply_elem<T, NC, AM_CHEB_LAST><<<g, kBlock, 0, s>>>(a); break;
+    default: k_apply_elem<T, NC, AM_RESID_CHEB0><<<g, kBlock, 0, s>>>(a); break;
+  }
+}
+
+#define INST(T)                                                                                   \
+  template void apply_full<T>(const ApplyArgs<T>&, const FixedMat<T, 4>&, int, int, cudaStream_t); \
+  template void apply_uu<T>(const ApplyArgs<T>&, const FixedMat<T, 4>&, int, int, cudaStream_t);   \
+  template void apply_pu<T>(const ApplyArgs<T>&, const FixedMat<T, 4>&, int, cudaStream_t);        \
+  template void apply_ss<T>(const ApplyArgs<T>&, const FixedMat<T, 1>&, int, int, cudaStream_t);   \
+  template void apply_elem<T, 1>(const ApplyArgs<T>&, int, int, cudaStream_t);                     \
+  template void apply_elem<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t);
+INST(float)
+INST(double)
+#undef INST
+
+}  // namespace cell

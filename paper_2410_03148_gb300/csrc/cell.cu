@@ -1,0 +1,999 @@
+// Solver orchestration and the C ABI (include/cell.h).
+//
+// Hot path per design: S1 set-up (material scaling, K0, S0, rho_e, multigrid
+// hierarchies), S2 right-hand sides, S3-S6 FP64-restarted SCP-GMRES (inner
+// Krylov cycles in FP32 or FP64), S7 null-space projection, S8 homogenised
+// tensors, S9 element sensitivities.  Everything runs on the caller's stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cell.h"
+#include "hostmath.h"
+#include "kernels.cuh"
+
+using cell::i64;
+using cell::kNvMax;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* what, cudaError_t e = cudaSuccess) {
+  g_last_error = what;
+  if (e != cudaSuccess) {
+    g_last_error += ": ";
+    g_last_error += cudaGetErrorString(e);
+  }
+}
+
+#define CK(call)                                     \
+  do {                                               \
+    cudaError_t _e = (call);                         \
+    if (_e != cudaSuccess) {                         \
+      set_error(#call, _e);                          \
+      return _e == cudaErrorMemoryAllocation ? CELL_ENOMEM : CELL_ECUDA; \
+    }                                                \
+  } while (0)
+
+#define CKS(call)                     \
+  do {                                \
+    int _s = (call);                  \
+    if (_s != CELL_OK) return _s;     \
+  } while (0)
+
+// Owned device allocations of a handle.
+struct Arena {
+  std::vector<void*> ptrs;
+  template <typename T>
+  int alloc(T** p, size_t n) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+      set_error("cudaMalloc", e);
+      return e == cudaErrorMemoryAllocation ? CELL_ENOMEM : CELL_ECUDA;
+    }
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return CELL_OK;
+  }
+  void release() {
+    for (void* p : ptrs) cudaFree(p);
+    ptrs.clear();
+  }
+};
+
+// Optional CUDA-event timing of kernel classes (full apply, block applies).
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<std::pair<int, int>> marks[2];  // (start event, stop event) per class
+  size_t used = 0;
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  int begin(cudaStream_t s) {
+    if (!on) return -1;
+    const int i = (int)used;
+    cudaEventRecord(get(), s);
+    return i;
+  }
+  void end(int cls, int i0, cudaStream_t s) {
+    if (!on || i0 < 0) return;
+    const int i1 = (int)used;
+    cudaEventRecord(get(), s);
+    marks[cls].push_back({i0, i1});
+  }
+  void collect(double* ms, int* cnt) {
+    for (int c = 0; c < 2; ++c) {
+      double t = 0.0;
+      for (auto& m : marks[c]) {
+        float f = 0.f;
+        cudaEventElapsedTime(&f, pool[m.first], pool[m.second]);
+        t += f;
+      }
+      ms[c] = t;
+      cnt[c] = (int)marks[c].size();
+      marks[c].clear();
+    }
+    used = 0;
+  }
+  ~Prof() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+enum { PROF_FULL = 0, PROF_BLOCK = 1 };
+
+template <typename T>
+struct Level {
+  int nx = 0, ny = 0, nz = 0;
+  i64 nn = 0;
+  T* ke = nullptr;       // per-element Galerkin matrices (levels >= 1), SoA
+  T* dinv = nullptr;     // [NC][nn]
+  double lmax = 1.0;
+  T *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *d2 = nullptr;  // [9][NC][nn]
+  T* dense = nullptr;    // coarsest: regularised inverse (n x n, symmetric)
+  int ndense = 0;
+  bool coarsest = false;
+};
+
+template <typename T>
+struct BlockMG {
+  int nc = 0;
+  std::vector<Level<T>> lv;
+  T* fixedm = nullptr;   // device copy of the level-0 element block ((8nc)^2)
+  std::vector<double> fixed_host;
+};
+
+template <typename T>
+struct Krylov {
+  int m = 0;
+  i64 len = 0;
+  T* V = nullptr;        // (m+1) x 9 x len
+  T* z = nullptr;        // 9 x len
+  T* u = nullptr;        // 9 x len
+  T* tphi = nullptr;     // 9 x nn (Schur block right-hand side)
+  T* ru = nullptr;       // 9 x 3nn (extra elastic V-cycles)
+  T* eu = nullptr;
+  T* rp = nullptr;       // 9 x nn (extra Schur V-cycles)
+  T* ep = nullptr;
+  cell::FixedMat<T, 4> K0;
+  cell::FixedMat<T, 1> S0;
+  const T* rho = nullptr;
+  BlockMG<T> mgu, mgp;
+};
+
+}  // namespace
+
+struct cell_handle {
+  cell_desc d{};
+  int nx = 0, ny = 0, nz = 0;
+  i64 nn = 0;
+  cudaStream_t st = nullptr;
+  double C0 = 1, k0 = 1;
+  double Cn[36], en[18], kn[9];
+  double h[3];
+  double K0[1024], S0[64], Z[288], F[288], H0e[81];
+  Arena arena;
+  float* rho32 = nullptr;
+  double* rho64 = nullptr;
+  double* K0dev = nullptr;
+  double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr;
+  double *partial = nullptr, *red = nullptr, *red2 = nullptr;
+  int nblk = 0;
+  // Krylov-scalar state (FP64, device)
+  double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *hcol = nullptr, *hnorm = nullptr;
+  double *resid = nullptr, *invscale = nullptr, *tolabs = nullptr, *ybuf = nullptr, *beta2 = nullptr;
+  double* ones = nullptr;
+  int *active = nullptr, *kcount = nullptr, *want = nullptr, *ranmask = nullptr;
+  Krylov<float> kf;
+  Krylov<double> kd;
+  bool solved = false;
+  Prof prof;
+  cell_stats last{};
+};
+
+namespace {
+
+template <typename T> Krylov<T>& kry(cell_handle* h);
+template <> Krylov<float>& kry<float>(cell_handle* h) { return h->kf; }
+template <> Krylov<double>& kry<double>(cell_handle* h) { return h->kd; }
+
+template <typename T> const T* rho_of(cell_handle* h);
+template <> const float* rho_of<float>(cell_handle* h) { return h->rho32; }
+template <> const double* rho_of<double>(cell_handle* h) { return h->rho64; }
+
+// ---------------------------------------------------------------------------
+// multigrid hierarchy
+// ---------------------------------------------------------------------------
+
+template <typename T, int NC>
+void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::ApplyArgs<T>& a0,
+                 const int* mask) {
+  cell::ApplyArgs<T> a = a0;
+  Level<T>& L = mg.lv[l];
+  a.nx = L.nx;
+  a.ny = L.ny;
+  a.nz = L.nz;
+  a.dinv = L.dinv;
+  a.active = mask;
+  Krylov<T>& K = kry<T>(h);
+  const int ip = h->prof.begin(h->st);
+  if (l == 0) {
+    a.rho = K.rho;
+    if (NC == 3) cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
+    else cell::apply_ss<T>(a, K.S0, mode, 9, h->st);
+  } else {
+    a.ke = L.ke;
+    cell::apply_elem<T, NC>(a, mode, 9, h->st);
+  }
+  h->prof.end(PROF_BLOCK, ip, h->st);
+}
+
+// Dense assembly of a level's operator on the host (coarsest level only).
+template <typename T, int NC>
+int assemble_dense(cell_handle* h, BlockMG<T>& mg, int l, std::vector<double>& A) {
+  Level<T>& L = mg.lv[l];
+  const int R = 8 * NC;
+  const i64 nn = L.nn;
+  const int n = (int)(NC * nn);
+  A.assign((size_t)n * n, 0.0);
+  std::vector<T> ke;
+  std::vector<double> rho;
+  if (l == 0) {
+    rho.resize(nn);
+    CK(cudaMemcpyAsync(rho.data(), h->rho64, nn * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  } else {
+    ke.resize((size_t)R * R * nn);
+    CK(cudaMemcpyAsync(ke.data(), L.ke, ke.size() * sizeof(T), cudaMemcpyDeviceToHost, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  for (i64 e = 0; e < nn; ++e) {
+    const int i = (int)(e % L.nx), j = (int)((e / L.nx) % L.ny), k = (int)(e / ((i64)L.nx * L.ny));
+    i64 node[8];
+    for (int a = 0; a < 8; ++a)
+      node[a] = (i + (a & 1)) % L.nx + (i64)L.nx * (((j + ((a >> 1) & 1)) % L.ny) + (i64)L.ny * ((k + (a >> 2)) % L.nz));
+    for (int a = 0; a < 8; ++a)
+      for (int c = 0; c < NC; ++c)
+        for (int b = 0; b < 8; ++b)
+          for (int dd = 0; dd < NC; ++dd) {
+            const int entry = (a * NC + c) * R + b * NC + dd;
+            const double v = l == 0 ? rho[e] * mg.fixed_host[entry] : (double)ke[(size_t)entry * nn + e];
+            A[(size_t)(c * nn + node[a]) * n + dd * nn + node[b]] += v;
+          }
+  }
+  return CELL_OK;
+}
+
+template <typename T, int NC>
+int build_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
+  const cell_options& o = h->d.opt;
+  const int R = 8 * NC;
+  mg.nc = NC;
+  mg.fixed_host.assign(fixed_block, fixed_block + R * R);
+  std::vector<T> fb(R * R);
+  for (int i = 0; i < R * R; ++i) fb[i] = (T)fixed_block[i];
+  CKS(h->arena.alloc(&mg.fixedm, R * R));
+  CK(cudaMemcpyAsync(mg.fixedm, fb.data(), R * R * sizeof(T), cudaMemcpyHostToDevice, h->st));
+  mg.lv.clear();
+  Level<T> L0;
+  L0.nx = h->nx;
+  L0.ny = h->ny;
+  L0.nz = h->nz;
+  L0.nn = h->nn;
+  L0.lmax = cellhost::jacobi_lmax(fixed_block, R);
+  mg.lv.push_back(L0);
+  // coarsen while every size is even, the coarse grid keeps >= 2 nodes per
+  // direction, and the level is still larger than the dense coarse target
+  while (true) {
+    Level<T>& P = mg.lv.back();
+    const bool even = (P.nx % 2 == 0) && (P.ny % 2 == 0) && (P.nz % 2 == 0);
+    const bool big = P.nn * NC > (i64)o.coarse_dofs;
+    if (!(even && big && P.nx >= 4 && P.ny >= 4 && P.nz >= 4)) break;
+    Level<T> C;
+    C.nx = P.nx / 2;
+    C.ny = P.ny / 2;
+    C.nz = P.nz / 2;
+    C.nn = (i64)C.nx * C.ny * C.nz;
+    mg.lv.push_back(C);
+  }
+  const int nl = (int)mg.lv.size();
+  unsigned int* lbits = nullptr;
+  CKS(h->arena.alloc(&lbits, 1));
+  for (int l = 0; l < nl; ++l) {
+    Level<T>& L = mg.lv[l];
+    CKS(h->arena.alloc(&L.dinv, NC * L.nn));
+    if (l > 0) {
+      Level<T>& F = mg.lv[l - 1];
+      CKS(h->arena.alloc(&L.ke, (size_t)R * R * L.nn));
+      if (l == 1) cell::galerkin<T, NC>(mg.fixedm, rho_of<T>(h), nullptr, L.ke, L.nx, L.ny, L.nz, h->st);
+      else cell::galerkin<T, NC>(nullptr, nullptr, F.ke, L.ke, L.nx, L.ny, L.nz, h->st);
+      cell::diag_inv<T, NC>(nullptr, nullptr, L.ke, L.dinv, L.nx, L.ny, L.nz, h->st);
+      CK(cudaMemsetAsync(lbits, 0, sizeof(unsigned), h->st));
+      cell::elem_lmax<T, NC>(L.ke, L.nn, lbits, h->st);
+      unsigned bits = 0;
+      CK(cudaMemcpyAsync(&bits, lbits, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+      CK(cudaStreamSynchronize(h->st));
+      float lf;
+      std::memcpy(&lf, &bits, sizeof(float));
+      L.lmax = lf > 0 ? (double)lf : 1.0;
+    } else {
+      cell::diag_inv<T, NC>(mg.fixedm, rho_of<T>(h), nullptr, L.dinv, L.nx, L.ny, L.nz, h->st);
+    }
+    const size_t wn = (size_t)9 * NC * L.nn;
+    if (l > 0) {
+      CKS(h->arena.alloc(&L.b, wn));
+      CKS(h->arena.alloc(&L.x, wn));
+    }
+    CKS(h->arena.alloc(&L.r, wn));
+    CKS(h->arena.alloc(&L.d, wn));
+    CKS(h->arena.alloc(&L.d2, wn));
+  }
+  Level<T>& Lc = mg.lv.back();
+  Lc.coarsest = true;
+  const i64 n = NC * Lc.nn;
+  if (n <= 3000) {
+    std::vector<double> A;
+    CKS((assemble_dense<T, NC>(h, mg, nl - 1, A)));
+    // regularise the null space (componentwise constants) and invert
+    double tr = 0.0;
+    for (i64 i = 0; i < n; ++i) tr += A[(size_t)i * n + i];
+    const double alpha = tr / (double)n;
+    for (int c = 0; c < NC; ++c)
+      for (i64 p = 0; p < Lc.nn; ++p)
+        for (i64 q = 0; q < Lc.nn; ++q) A[(size_t)(c * Lc.nn + p) * n + c * Lc.nn + q] += alpha / (double)Lc.nn;
+    if (cellhost::spd_inverse(A.data(), (int)n) != 0) {
+      set_error("coarsest multigrid level is not positive definite (rho must be > 0)");
+      return CELL_EINVAL;
+    }
+    std::vector<T> At(A.size());
+    for (size_t i = 0; i < A.size(); ++i) At[i] = (T)A[i];
+    CKS(h->arena.alloc(&Lc.dense, At.size()));
+    CK(cudaMemcpyAsync(Lc.dense, At.data(), At.size() * sizeof(T), cudaMemcpyHostToDevice, h->st));
+    Lc.ndense = (int)n;
+    CK(cudaStreamSynchronize(h->st));
+  }
+  return CELL_OK;
+}
+
+struct ChebCoef {
+  double theta, delta, sigma, rho0;
+};
+
+inline ChebCoef cheb_coef(const cell_options& o, double lmax) {
+  const double hi = lmax * o.cheb_hi, lo = hi * o.cheb_lo;
+  ChebCoef c;
+  c.theta = 0.5 * (hi + lo);
+  c.delta = 0.5 * (hi - lo);
+  c.sigma = c.theta / c.delta;
+  c.rho0 = 1.0 / c.sigma;
+  return c;
+}
+
+// x = V-cycle approximation of A_l^-1 b (zero initial guess).
+template <typename T, int NC>
+void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64 xs, const int* mask) {
+  const cell_options& o = h->d.opt;
+  Level<T>& L = mg.lv[l];
+  const i64 ws = NC * L.nn;
+  if (L.coarsest && L.dense) {
+    cell::dense_solve<T>(L.dense, L.ndense, b, bs, x, xs, L.nn, NC, 9, mask, h->st);
+    return;
+  }
+  const int deg = L.coarsest ? std::max(8, 4 * o.cheb_degree) : o.cheb_degree;
+  const ChebCoef cc = cheb_coef(o, L.lmax);
+  cell::ApplyArgs<T> a{};
+  // pre-smoothing from x = 0
+  cell::cheb_init<T, NC>(b, bs, L.r, ws, L.d, ws, L.dinv, (T)(1.0 / cc.theta), L.nn, 9, mask, h->st);
+  double rp = cc.rho0;
+  T* d = L.d;
+  T* d2 = L.d2;
+  int zero = 1;
+  for (int k = 1; k < deg; ++k) {
+    const double rk = 1.0 / (2.0 * cc.sigma - rp);
+    a = cell::ApplyArgs<T>{};
+    a.x = d; a.xs = ws; a.y = L.r; a.ys = ws; a.sol = x; a.ss = xs; a.dout = d2; a.ds = ws;
+    a.c1 = (T)(rk * rp); a.c2 = (T)(2.0 * rk / cc.delta); a.sol_zero = zero;
+    level_apply<T, NC>(h, mg, l, cell::AM_CHEB, a, mask);
+    std::swap(d, d2);
+    zero = 0;
+    rp = rk;
+  }
+  a = cell::ApplyArgs<T>{};
+  a.x = d; a.xs = ws; a.y = L.r; a.ys = ws; a.sol = x; a.ss = xs; a.sol_zero = zero;
+  level_apply<T, NC>(h, mg, l, cell::AM_CHEB_LAST, a, mask);
+  if (L.coarsest) return;
+  Level<T>& C = mg.lv[l + 1];
+  const i64 cs = NC * C.nn;
+  cell::restrict_fw<T, NC>(L.r, ws, C.b, cs, L.nx, L.ny, L.nz, 9, mask, h->st);
+  vcycle<T, NC>(h, mg, l + 1, C.b, cs, C.x, cs, mask);
+  cell::prolong_add<T, NC>(C.x, cs, x, xs, L.nx, L.ny, L.nz, 9, mask, h->st);
+  // post-smoothing
+  a = cell::ApplyArgs<T>{};
+  a.x = x; a.xs = xs; a.b = b; a.bs = bs; a.y = L.r; a.ys = ws; a.dout = L.d; a.ds = ws;
+  a.c2 = (T)(1.0 / cc.theta);
+  level_apply<T, NC>(h, mg, l, cell::AM_RESID_CHEB0, a, mask);
+  rp = cc.rho0;
+  d = L.d;
+  d2 = L.d2;
+  for (int k = 1; k < deg; ++k) {
+    const double rk = 1.0 / (2.0 * cc.sigma - rp);
+    a = cell::ApplyArgs<T>{};
+    a.x = d; a.xs = ws; a.y = L.r; a.ys = ws; a.sol = x; a.ss = xs; a.dout = d2; a.ds = ws;
+    a.c1 = (T)(rk * rp); a.c2 = (T)(2.0 * rk / cc.delta); a.sol_zero = 0;
+    level_apply<T, NC>(h, mg, l, cell::AM_CHEB, a, mask);
+    std::swap(d, d2);
+    rp = rk;
+  }
+  cell::axpy_view<T, NC>(x, xs, d, ws, L.nn, 9, mask, h->st);
+}
+
+// k V-cycles by residual correction: x ~ A^-1 b.
+template <typename T, int NC>
+void block_solve(cell_handle* h, BlockMG<T>& mg, int cycles, const T* b, i64 bs, T* x, i64 xs,
+                 T* rwork, T* ework, const int* mask) {
+  vcycle<T, NC>(h, mg, 0, b, bs, x, xs, mask);
+  const i64 ws = NC * h->nn;
+  for (int c = 1; c < cycles; ++c) {
+    cell::ApplyArgs<T> a{};
+    a.x = x; a.xs = xs; a.y = rwork; a.ys = ws; a.b = b; a.bs = bs; a.alpha = T(-1); a.beta = T(1);
+    level_apply<T, NC>(h, mg, 0, cell::AM_LINEAR, a, mask);
+    vcycle<T, NC>(h, mg, 0, rwork, ws, ework, ws, mask);
+    cell::axpy_view<T, NC>(x, xs, ework, ws, h->nn, 9, mask, h->st);
+  }
+}
+
+// z = P_SCP^-1 v (§2.5.3): z_u ~ A^-1 v_u, z_phi ~ Sbar^-1 (v_phi + B z_u).
+template <typename T>
+void precond(cell_handle* h, const T* v, T* z, const int* mask) {
+  Krylov<T>& K = kry<T>(h);
+  const i64 nn = h->nn, len = K.len;
+  block_solve<T, 3>(h, K.mgu, h->d.opt.vcycles_u, v, len, z, len, K.ru, K.eu, mask);
+  cell::ApplyArgs<T> a{};
+  a.x = z; a.xs = len; a.y = K.tphi; a.ys = nn; a.b = v + 3 * nn; a.bs = len;
+  a.alpha = T(1); a.beta = T(1); a.rho = K.rho; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+  a.active = mask;
+  cell::apply_pu<T>(a, K.K0, 9, h->st);
+  block_solve<T, 1>(h, K.mgp, h->d.opt.vcycles_phi, K.tphi, nn, z + 3 * nn, len, K.rp, K.ep, mask);
+}
+
+template <typename T>
+void apply_full_T(cell_handle* h, const T* x, i64 xs, T* y, i64 ys, const T* b, i64 bs, T alpha,
+                  T beta, const int* mask, int nrhs) {
+  cell::ApplyArgs<T> a{};
+  a.x = x; a.xs = xs; a.y = y; a.ys = ys; a.b = b; a.bs = bs; a.alpha = alpha; a.beta = beta;
+  a.rho = rho_of<T>(h); a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.active = mask;
+  const int ip = h->prof.begin(h->st);
+  if constexpr (sizeof(T) == 4) cell::apply_full<T>(a, h->kf.K0, cell::AM_LINEAR, nrhs, h->st);
+  else cell::apply_full<T>(a, h->kd.K0, cell::AM_LINEAR, nrhs, h->st);
+  h->prof.end(PROF_FULL, ip, h->st);
+}
+
+template <typename T>
+int setup_krylov(cell_handle* h) {
+  Krylov<T>& K = kry<T>(h);
+  const cell_options& o = h->d.opt;
+  K.m = o.restart;
+  K.len = 4 * h->nn;
+  K.rho = rho_of<T>(h);
+  for (int i = 0; i < 1024; ++i) K.K0.k[i] = (T)h->K0[i];
+  for (int i = 0; i < 64; ++i) K.S0.k[i] = (T)h->S0[i];
+  CKS(h->arena.alloc(&K.V, (size_t)(K.m + 1) * 9 * K.len));
+  CKS(h->arena.alloc(&K.z, (size_t)9 * K.len));
+  CKS(h->arena.alloc(&K.u, (size_t)9 * K.len));
+  CKS(h->arena.alloc(&K.tphi, (size_t)9 * h->nn));
+  if (o.vcycles_u > 1) {
+    CKS(h->arena.alloc(&K.ru, (size_t)27 * h->nn));
+    CKS(h->arena.alloc(&K.eu, (size_t)27 * h->nn));
+  }
+  if (o.vcycles_phi > 1) {
+    CKS(h->arena.alloc(&K.rp, (size_t)9 * h->nn));
+    CKS(h->arena.alloc(&K.ep, (size_t)9 * h->nn));
+  }
+  // level-0 blocks of the preconditioner: A_e (24x24 u-block of K0), S0
+  std::vector<double> Auu(576);
+  for (int a = 0; a < 8; ++a)
+    for (int c = 0; c < 3; ++c)
+      for (int b = 0; b < 8; ++b)
+        for (int d = 0; d < 3; ++d) Auu[(a * 3 + c) * 24 + b * 3 + d] = h->K0[(4 * a + c) * 32 + 4 * b + d];
+  CKS((build_mg<T, 3>(h, K.mgu, Auu.data())));
+  CKS((build_mg<T, 1>(h, K.mgp, h->S0)));
+  return CELL_OK;
+}
+
+// One restarted GMRES cycle (<= m iterations) on Ahat d = r64 for the loads
+// in h->want, in precision T; on return x64 += d.
+template <typename T>
+int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
+  Krylov<T>& K = kry<T>(h);
+  const int m = K.m;
+  const i64 len = K.len;
+  const i64 vstride = 9 * len;
+  cudaStream_t s = h->st;
+  const int nblk = h->nblk;
+  // beta^2 = |r|^2
+  cell::multidot<double>(h->r64, 0, len, 1, h->r64, len, len, h->partial, nblk, kNvMax, 9, h->want, s);
+  cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->beta2, 0, 9, h->want, s);
+  CK(cudaMemcpyAsync(h->tolabs, tolabs_host, 9 * sizeof(double), cudaMemcpyHostToDevice, s));
+  cell::start_cycle(h->beta2, h->g, m, h->active, h->want, h->resid, h->invscale, h->tolabs, h->kcount, 9, s);
+  CK(cudaMemcpyAsync(h->ranmask, h->active, 9 * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  if constexpr (sizeof(T) == 4) {
+    cell::to_f32_scaled(h->r64, len, reinterpret_cast<float*>(K.V), len, len, h->invscale, 9, h->ranmask, s);
+  } else {
+    CK(cudaMemcpyAsync(K.V, h->r64, 9 * len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    cell::scale_vec<T>(K.V, len, len, h->invscale, 9, s);
+  }
+  int ran[9];
+  CK(cudaMemcpyAsync(ran, h->ranmask, sizeof(ran), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  bool any = false;
+  for (int q = 0; q < 9; ++q) any = any || ran[q];
+  if (!any) return CELL_OK;
+  int j = 0;
+  for (; j < m; ++j) {
+    T* vj = K.V + (i64)j * vstride;
+    T* w = K.V + (i64)(j + 1) * vstride;
+    precond<T>(h, vj, K.z, h->active);
+    apply_full_T<T>(h, K.z, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
+    // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2 (with |w|^2)
+    cell::multidot<T>(K.V, vstride, len, j + 1, w, len, len, h->partial, nblk, kNvMax, 9, h->active, s);
+    cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->hcol, 0, 9, h->active, s);
+    cell::update<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, 1, h->partial, nblk, 9, h->active, s);
+    cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->ybuf, 0, 9, h->active, s);
+    cell::update<T>(K.V, vstride, len, j + 1, h->ybuf, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->active, s);
+    cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->active, s);
+    // hcol += second-pass coefficients (a one-block "reduction" of ybuf)
+    cell::reduce_partials(h->ybuf, 1, j + 1, kNvMax, h->hcol, 1, 9, h->active, s);
+    cell::givens_step(h->H, h->cs, h->sn, h->g, h->hcol, h->hnorm, j, m, h->active, h->resid,
+                      h->tolabs, h->invscale, h->kcount, 9, s);
+    cell::scale_vec<T>(w, len, len, h->invscale, 9, s);
+    int act[9];
+    CK(cudaMemcpyAsync(act, h->active, sizeof(act), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    bool more = false;
+    for (int q = 0; q < 9; ++q) more = more || act[q];
+    if (!more) break;
+  }
+  cell::backsolve(h->H, h->g, h->kcount, m, h->ybuf, 9, h->ranmask, s);
+  cell::lincomb<T>(K.V, vstride, len, h->ybuf, h->kcount, kNvMax, K.u, len, len, 9, h->ranmask, s);
+  precond<T>(h, K.u, K.z, h->ranmask);
+  cell::axpy_f64<T>(h->x64, len, K.z, len, len, h->ones, 9, h->ranmask, s);
+  int kc[9];
+  CK(cudaMemcpyAsync(kc, h->kcount, sizeof(kc), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  for (int q = 0; q < 9; ++q)
+    if (ran[q]) iters[q] += kc[q];
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
+int check_options(const cell_options& o) {
+  if (!(o.tol > 0.0) || !(o.tol < 1.0)) return CELL_EINVAL;
+  if (o.restart < 1 || o.restart > kNvMax - 1) return CELL_EINVAL;
+  if (o.max_iter < 1) return CELL_EINVAL;
+  if (o.precision != CELL_FP64 && o.precision != CELL_MIXED_FP32) return CELL_EINVAL;
+  if (o.precision == CELL_MIXED_FP32 && !(o.inner_tol > 0.0 && o.inner_tol < 1.0)) return CELL_EINVAL;
+  if (o.max_refine < 1) return CELL_EINVAL;
+  if (o.vcycles_u < 1 || o.vcycles_phi < 1 || o.cheb_degree < 1 || o.cheb_degree > 16) return CELL_EINVAL;
+  if (!(o.cheb_lo > 0.0 && o.cheb_lo < 1.0) || !(o.cheb_hi > 0.0)) return CELL_EINVAL;
+  if (!(o.schur_shift >= 0.0) || o.coarse_dofs < 1) return CELL_EINVAL;
+  if ((o.load_mask & 0x1FF) == 0 || (o.load_mask & ~0x1FF)) return CELL_EINVAL;
+  return CELL_OK;
+}
+
+int setup_impl(const cell_desc* d, cell_handle* h) {
+  h->d = *d;
+  h->d.input = nullptr;
+  h->nx = d->nx;
+  h->ny = d->ny;
+  h->nz = d->nz;
+  h->nn = (i64)d->nx * d->ny * d->nz;
+  h->st = static_cast<cudaStream_t>(d->stream);
+  h->prof.on = d->opt.profile != 0;
+  cellhost::nondimensionalise(d->C, d->e, d->kappa, h->Cn, h->en, h->kn, &h->C0, &h->k0);
+  h->h[0] = 1.0 / d->nx;
+  h->h[1] = 1.0 / d->ny;
+  h->h[2] = 1.0 / d->nz;
+  cellhost::element_matrix(h->Cn, h->en, h->kn, h->h, h->K0);
+  if (cellhost::local_schur(h->K0, d->opt.schur_shift, h->S0) != 0) {
+    set_error("elastic element block is not positive definite (check C)");
+    return CELL_EINVAL;
+  }
+  cellhost::affine_loads(h->h, h->Z);
+  for (int a = 0; a < 32; ++a)
+    for (int I = 0; I < 9; ++I) {
+      double s = 0.0;
+      for (int b = 0; b < 32; ++b) s += h->K0[a * 32 + b] * h->Z[b * 9 + I];
+      h->F[a * 9 + I] = s;
+    }
+  for (int I = 0; I < 9; ++I)
+    for (int J = 0; J < 9; ++J) {
+      double s = 0.0;
+      for (int a = 0; a < 32; ++a) s += h->Z[a * 9 + I] * h->F[a * 9 + J];
+      h->H0e[I * 9 + J] = s;
+    }
+  const i64 nn = h->nn;
+  Arena& A = h->arena;
+  CKS(A.alloc(&h->rho32, nn));
+  CKS(A.alloc(&h->rho64, nn));
+  CKS(A.alloc(&h->K0dev, 1024));
+  CK(cudaMemcpyAsync(h->K0dev, h->K0, 1024 * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  int* bad = nullptr;
+  CKS(A.alloc(&bad, 1));
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), h->st));
+  if (d->input_kind == CELL_INPUT_PHI) {
+    const double eta = d->eta > 0 ? d->eta : 2.0 * std::max(h->h[0], std::max(h->h[1], h->h[2]));
+    if (d->input_dtype == CELL_F32)
+      cell::ersatz<float>(static_cast<const float*>(d->input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
+    else
+      cell::ersatz<double>(static_cast<const double*>(d->input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
+  } else {
+    if (d->input_dtype == CELL_F32)
+      cell::rho_copy<float>(static_cast<const float*>(d->input), nn, h->rho32, h->rho64, bad, h->st);
+    else
+      cell::rho_copy<double>(static_cast<const double*>(d->input), nn, h->rho32, h->rho64, bad, h->st);
+  }
+  int nbad = 0;
+  CK(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (nbad) {
+    set_error("rho input has non-positive or non-finite values");
+    return CELL_EINVAL;
+  }
+  // vectors and Krylov scalars
+  const i64 len = 4 * nn;
+  CKS(A.alloc(&h->b64, 9 * len));
+  CKS(A.alloc(&h->x64, 9 * len));
+  CKS(A.alloc(&h->r64, 9 * len));
+  h->nblk = (int)std::min<i64>(1024, std::max<i64>(1, (len + 4095) / 4096));
+  CKS(A.alloc(&h->partial, (size_t)9 * 4 * h->nblk * kNvMax));
+  CKS(A.alloc(&h->red, 9 * kNvMax));
+  CKS(A.alloc(&h->red2, 9 * kNvMax));
+  const int m = d->opt.restart;
+  CKS(A.alloc(&h->H, (size_t)9 * (m + 1) * m));
+  CKS(A.alloc(&h->cs, 9 * m));
+  CKS(A.alloc(&h->sn, 9 * m));
+  CKS(A.alloc(&h->g, 9 * (m + 1)));
+  CKS(A.alloc(&h->hcol, 9 * kNvMax));
+  CKS(A.alloc(&h->hnorm, 9 * kNvMax));
+  CKS(A.alloc(&h->ybuf, 9 * kNvMax));
+  CKS(A.alloc(&h->beta2, 9 * kNvMax));
+  CKS(A.alloc(&h->resid, 9));
+  CKS(A.alloc(&h->invscale, 9));
+  CKS(A.alloc(&h->tolabs, 9));
+  CKS(A.alloc(&h->ones, 9));
+  {
+    const double one9[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+    CK(cudaMemcpyAsync(h->ones, one9, sizeof(one9), cudaMemcpyHostToDevice, h->st));
+  }
+  CKS(A.alloc(&h->active, 9));
+  CKS(A.alloc(&h->kcount, 9));
+  CKS(A.alloc(&h->want, 9));
+  CKS(A.alloc(&h->ranmask, 9));
+  CK(cudaMemsetAsync(h->x64, 0, 9 * len * sizeof(double), h->st));
+  // the FP64 operator serves the refinement residual in every precision mode
+  std::memcpy(h->kd.K0.k, h->K0, sizeof(h->kd.K0.k));
+  std::memcpy(h->kd.S0.k, h->S0, sizeof(h->kd.S0.k));
+  h->kd.rho = h->rho64;
+  if (d->opt.precision == CELL_MIXED_FP32) CKS(setup_krylov<float>(h));
+  else CKS(setup_krylov<double>(h));
+  CK(cudaStreamSynchronize(h->st));
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
+template <typename T>
+int solve_impl(cell_handle* h, cell_stats* st) {
+  const cell_options& o = h->d.opt;
+  cudaStream_t s = h->st;
+  const i64 len = 4 * h->nn;
+  const int nblk = h->nblk;
+  cell_stats S{};
+  auto t0 = std::chrono::steady_clock::now();
+  cell::RhsParams RP;
+  std::memcpy(RP.F, h->F, sizeof(RP.F));
+  cell::rhs9(h->rho64, RP, o.load_mask, h->b64, h->nx, h->ny, h->nz, s);
+  CK(cudaMemsetAsync(h->x64, 0, 9 * len * sizeof(double), s));
+  double bn2[9], rn2[9];
+  cell::multidot<double>(h->b64, 0, len, 1, h->b64, len, len, h->partial, nblk, kNvMax, 9, nullptr, s);
+  cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->red, 0, 9, nullptr, s);
+  std::vector<double> tmp(9 * kNvMax);
+  CK(cudaMemcpyAsync(tmp.data(), h->red, 9 * kNvMax * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(h->r64, h->b64, 9 * len * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  for (int q = 0; q < 9; ++q) bn2[q] = tmp[q * kNvMax];
+  int status = CELL_OK;
+  int refine = 0;
+  while (true) {
+    cell::multidot<double>(h->r64, 0, len, 1, h->r64, len, len, h->partial, nblk, kNvMax, 9, nullptr, s);
+    cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->red, 0, 9, nullptr, s);
+    CK(cudaMemcpyAsync(tmp.data(), h->red, 9 * kNvMax * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    int want[9];
+    double tolabs[9];
+    bool any = false;
+    int maxit = 0;
+    for (int q = 0; q < 9; ++q) {
+      rn2[q] = tmp[q * kNvMax];
+      const double bn = std::sqrt(bn2[q]), rn = std::sqrt(rn2[q]);
+      S.rel_residual[q] = bn > 0 ? rn / bn : 0.0;
+      want[q] = ((o.load_mask >> q) & 1) && bn > 0 && rn > o.tol * bn;
+      any = any || want[q];
+      maxit = std::max(maxit, S.iters[q]);
+      const double inner = sizeof(T) == 4 ? o.inner_tol : o.tol * 0.5;
+      tolabs[q] = std::max(inner * rn, 0.5 * o.tol * bn);
+    }
+    if (!any) break;
+    if (refine >= o.max_refine || maxit >= o.max_iter) {
+      status = CELL_ENOTCONV;
+      break;
+    }
+    CK(cudaMemcpyAsync(h->want, want, sizeof(want), cudaMemcpyHostToDevice, s));
+    CKS(gmres_cycle<T>(h, tolabs, S.iters));
+    ++refine;
+    // FP64 residual of the updated iterate: r = bhat - Ahat x
+    apply_full_T<double>(h, h->x64, len, h->r64, len, h->b64, len, -1.0, 1.0, nullptr, 9);
+  }
+  // null-space projection (mean displacement and potential per load)
+  cell::comp_sums(h->x64, h->nn, 9, h->partial, nblk, h->red2, s);
+  cell::sub_means(h->x64, h->nn, 9, h->red2, s);
+  CK(cudaStreamSynchronize(s));
+  CK(cudaGetLastError());
+  auto t1 = std::chrono::steady_clock::now();
+  S.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+  S.refinements = refine;
+  S.status = status;
+  S.nlevels_u = (int)kry<T>(h).mgu.lv.size();
+  S.nlevels_phi = (int)kry<T>(h).mgp.lv.size();
+  if (h->prof.on) {
+    double ms[2];
+    int cnt[2];
+    h->prof.collect(ms, cnt);
+    S.apply_ms = ms[0];
+    S.apply_count = cnt[0];
+    S.smooth_ms = ms[1];
+    S.smooth_count = cnt[1];
+  }
+  h->solved = (status == CELL_OK);
+  h->last = S;
+  if (st) *st = S;
+  return status;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+void cell_default_options(cell_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->restart = 30;
+  o->max_iter = 400;
+  o->precision = CELL_MIXED_FP32;
+  o->inner_tol = 1e-4;
+  o->max_refine = 40;
+  o->vcycles_u = 1;
+  o->vcycles_phi = 1;
+  o->cheb_degree = 3;
+  o->cheb_lo = 0.1;
+  o->cheb_hi = 1.0;
+  o->schur_shift = 1e-10;
+  o->coarse_dofs = 200;
+  o->load_mask = 0x1FF;
+  o->profile = 0;
+}
+
+int cell_setup(const cell_desc* d, cell_handle** out) {
+  if (!d || !out) return CELL_EINVAL;
+  *out = nullptr;
+  if (d->nx < 2 || d->ny < 2 || d->nz < 2) return CELL_EINVAL;
+  if ((double)d->nx * d->ny * d->nz > 4.0e8) return CELL_EINVAL;
+  if (!d->input) return CELL_EINVAL;
+  if (d->input_kind != CELL_INPUT_RHO && d->input_kind != CELL_INPUT_PHI) return CELL_EINVAL;
+  if (d->input_dtype != CELL_F32 && d->input_dtype != CELL_F64) return CELL_EINVAL;
+  if (d->input_kind == CELL_INPUT_PHI && !(d->rho_void > 0.0 && d->rho_void <= 1.0)) return CELL_EINVAL;
+  for (int i = 0; i < 36; ++i) if (!std::isfinite(d->C[i])) return CELL_EINVAL;
+  for (int i = 0; i < 18; ++i) if (!std::isfinite(d->e[i])) return CELL_EINVAL;
+  for (int i = 0; i < 9; ++i) if (!std::isfinite(d->kappa[i])) return CELL_EINVAL;
+  if (check_options(d->opt) != CELL_OK) return CELL_EINVAL;
+  cell_handle* h = new cell_handle();
+  const int s = setup_impl(d, h);
+  if (s != CELL_OK) {
+    cudaStreamSynchronize(h->st);
+    h->arena.release();
+    delete h;
+    return s;
+  }
+  *out = h;
+  return CELL_OK;
+}
+
+int cell_solve(cell_handle* h, cell_stats* st) {
+  if (!h) return CELL_EINVAL;
+  if (h->d.opt.precision == CELL_MIXED_FP32) return solve_impl<float>(h, st);
+  return solve_impl<double>(h, st);
+}
+
+int cell_homogenise(cell_handle* h, double CH[36], double eH[18], double kH[9]) {
+  if (!h || !CH || !eH || !kH) return CELL_EINVAL;
+  if (!h->solved || h->d.opt.load_mask != 0x1FF) return CELL_ESTATE;
+  cudaStream_t s = h->st;
+  const int nblk = h->nblk;
+  double G1[81], G2[81], srho;
+  cell::sum_reduce(h->rho64, h->nn, h->partial, nblk, h->red, s);
+  CK(cudaMemcpyAsync(&srho, h->red, sizeof(double), cudaMemcpyDeviceToHost, s));
+  cell::gram9(h->b64, h->x64, h->nn, h->partial, nblk, h->red, s);
+  CK(cudaMemcpyAsync(G1, h->red, sizeof(G1), cudaMemcpyDeviceToHost, s));
+  cell::gram9(h->x64, h->r64, h->nn, h->partial, nblk, h->red2, s);
+  CK(cudaMemcpyAsync(G2, h->red2, sizeof(G2), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  // energy form: H = sum rho H0e - b.y - y.r   (H0e = Zbar^T K0 Zbar)
+  double H[81];
+  for (int i = 0; i < 81; ++i) H[i] = srho * h->H0e[i] - G1[i] - G2[i];
+  for (int I = 0; I < 9; ++I)
+    for (int J = I + 1; J < 9; ++J) {
+      const double v = 0.5 * (H[I * 9 + J] + H[J * 9 + I]);
+      H[I * 9 + J] = H[J * 9 + I] = v;
+    }
+  const double se = std::sqrt(h->C0 * h->k0);
+  for (int p = 0; p < 6; ++p)
+    for (int q = 0; q < 6; ++q) CH[p * 6 + q] = h->C0 * H[p * 9 + q];
+  for (int i = 0; i < 3; ++i)
+    for (int p = 0; p < 6; ++p) eH[i * 6 + p] = -se * H[(6 + i) * 9 + p];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) kH[i * 3 + j] = -h->k0 * H[(6 + i) * 9 + 6 + j];
+  return CELL_OK;
+}
+
+int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18], const double dk[9],
+                     void* g, int dtype) {
+  if (!h || !g || (dtype != CELL_F32 && dtype != CELL_F64)) return CELL_EINVAL;
+  if (!h->solved) return CELL_ESTATE;
+  cell::SensParams P;
+  std::memcpy(P.Z, h->Z, sizeof(P.Z));
+  std::memset(P.G, 0, sizeof(P.G));
+  const double se = std::sqrt(h->C0 * h->k0);
+  for (int p = 0; p < 6; ++p)
+    for (int q = 0; q < 6; ++q) P.G[p * 9 + q] = dC ? h->C0 * dC[p * 6 + q] : 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int p = 0; p < 6; ++p) {
+      const double v = de ? -0.5 * se * de[i * 6 + p] : 0.0;
+      P.G[(6 + i) * 9 + p] = v;
+      P.G[p * 9 + 6 + i] = v;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) P.G[(6 + i) * 9 + 6 + j] = dk ? -h->k0 * dk[i * 3 + j] : 0.0;
+  if (dtype == CELL_F32)
+    cell::sensitivity<float>(h->x64, h->rho64, h->K0dev, P, static_cast<float*>(g), h->nx, h->ny, h->nz, 0, h->st);
+  else
+    cell::sensitivity<double>(h->x64, h->rho64, h->K0dev, P, static_cast<double*>(g), h->nx, h->ny, h->nz, 0, h->st);
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
+int cell_dh(const double C[36], const double e[18], double* dh, double dC[36], double de[18]) {
+  if (!C || !e || !dh) return CELL_EINVAL;
+  double S[36];
+  std::memcpy(S, C, sizeof(S));
+  // general 6x6 inverse by Gauss-Jordan with partial pivoting
+  double I6[36] = {0};
+  for (int i = 0; i < 6; ++i) I6[i * 6 + i] = 1.0;
+  for (int k = 0; k < 6; ++k) {
+    int p = k;
+    for (int i = k + 1; i < 6; ++i)
+      if (std::fabs(S[i * 6 + k]) > std::fabs(S[p * 6 + k])) p = i;
+    if (!(std::fabs(S[p * 6 + k]) > 0.0)) return CELL_EINVAL;
+    for (int j = 0; j < 6; ++j) {
+      std::swap(S[k * 6 + j], S[p * 6 + j]);
+      std::swap(I6[k * 6 + j], I6[p * 6 + j]);
+    }
+    const double piv = S[k * 6 + k];
+    for (int j = 0; j < 6; ++j) {
+      S[k * 6 + j] /= piv;
+      I6[k * 6 + j] /= piv;
+    }
+    for (int i = 0; i < 6; ++i) {
+      if (i == k) continue;
+      const double f = S[i * 6 + k];
+      for (int j = 0; j < 6; ++j) {
+        S[i * 6 + j] -= f * S[k * 6 + j];
+        I6[i * 6 + j] -= f * I6[k * 6 + j];
+      }
+    }
+  }
+  // I6 = C^-1 = S (compliance); d_h = e_3 . S m, m = (1,1,1,0,0,0)
+  double w[6], se3[6];
+  for (int i = 0; i < 6; ++i) {
+    w[i] = I6[i * 6 + 0] + I6[i * 6 + 1] + I6[i * 6 + 2];
+    double t = 0.0;
+    for (int j = 0; j < 6; ++j) t += I6[i * 6 + j] * e[12 + j];
+    se3[i] = t;
+  }
+  double v = 0.0;
+  for (int p = 0; p < 6; ++p) v += e[12 + p] * w[p];
+  *dh = v;
+  if (dC)
+    for (int i = 0; i < 6; ++i)
+      for (int j = 0; j < 6; ++j) dC[i * 6 + j] = -se3[i] * w[j];
+  if (de) {
+    for (int i = 0; i < 18; ++i) de[i] = 0.0;
+    for (int p = 0; p < 6; ++p) de[12 + p] = w[p];
+  }
+  return CELL_OK;
+}
+
+int cell_get_solution(cell_handle* h, double* out) {
+  if (!h || !out) return CELL_EINVAL;
+  CK(cudaMemcpyAsync(out, h->x64, 9 * 4 * h->nn * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  return CELL_OK;
+}
+
+int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype) {
+  if (!h || !x || !y || nrhs < 1 || nrhs > 65535) return CELL_EINVAL;
+  const i64 len = 4 * h->nn;
+  if (dtype == CELL_F32) {
+    cell::ApplyArgs<float> a{};
+    a.x = static_cast<const float*>(x); a.xs = len; a.y = static_cast<float*>(y); a.ys = len;
+    a.alpha = 1.f; a.rho = h->rho32; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    cell::FixedMat<float, 4> M;
+    for (int i = 0; i < 1024; ++i) M.k[i] = (float)h->K0[i];
+    cell::apply_full<float>(a, M, cell::AM_LINEAR, nrhs, h->st);
+  } else if (dtype == CELL_F64) {
+    cell::ApplyArgs<double> a{};
+    a.x = static_cast<const double*>(x); a.xs = len; a.y = static_cast<double*>(y); a.ys = len;
+    a.alpha = 1.0; a.rho = h->rho64; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    cell::FixedMat<double, 4> M;
+    std::memcpy(M.k, h->K0, sizeof(M.k));
+    cell::apply_full<double>(a, M, cell::AM_LINEAR, nrhs, h->st);
+  } else {
+    return CELL_EINVAL;
+  }
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
+int cell_rhs(cell_handle* h, double* out) {
+  if (!h || !out) return CELL_EINVAL;
+  cell::RhsParams RP;
+  std::memcpy(RP.F, h->F, sizeof(RP.F));
+  cell::rhs9(h->rho64, RP, 0x1FF, out, h->nx, h->ny, h->nz, h->st);
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
+int cell_get_rho(cell_handle* h, double* out) {
+  if (!h || !out) return CELL_EINVAL;
+  CK(cudaMemcpyAsync(out, h->rho64, h->nn * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  return CELL_OK;
+}
+
+int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]) {
+  if (!d || !K0 || !S0 || d->nx < 1 || d->ny < 1 || d->nz < 1) return CELL_EINVAL;
+  double Cn[36], en[18], kn[9], C0, k0;
+  cellhost::nondimensionalise(d->C, d->e, d->kappa, Cn, en, kn, &C0, &k0);
+  const double hh[3] = {1.0 / d->nx, 1.0 / d->ny, 1.0 / d->nz};
+  cellhost::element_matrix(Cn, en, kn, hh, K0);
+  if (cellhost::local_schur(K0, d->opt.schur_shift, S0) != 0) return CELL_EINVAL;
+  return CELL_OK;
+}
+
+void cell_destroy(cell_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->st);
+  h->arena.release();
+  delete h;
+}
+
+const char* cell_status_str(int s) {
+  switch (s) {
+    case CELL_OK: return "ok";
+    case CELL_EINVAL: return "invalid argument";
+    case CELL_ENOMEM: return "out of device memory";
+    case CELL_ENOTCONV: return "solver did not reach the tolerance";
+    case CELL_ETIMEOUT: return "bounded device wait expired";
+    case CELL_ECUDA: return "CUDA runtime error";
+    case CELL_ESTATE: return "call out of order";
+    default: return "unknown status";
+  }
+}
+
+const char* cell_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

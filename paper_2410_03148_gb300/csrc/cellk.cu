@@ -1,0 +1,269 @@
+// Cell-level kernels: the ersatz map from the level set (§2.6), the nine
+// right-hand sides (§2.2), reductions for the null-space projection and the
+// homogenised tensors (Eqs. hom_C, hom_e, hom_kappa), and the element-wise
+// sensitivity quadratic forms.
+#include "kernels.cuh"
+
+namespace cell {
+
+namespace {
+
+constexpr int kB = 256;
+constexpr int kWarps = kB / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < kWarps ? sh[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// rho_e = 1 - (1 - rho_void) H_eta(phi_e), phi_e = mean of the 8 nodal values.
+template <typename Tin>
+__global__ void k_ersatz(const Tin* __restrict__ phi, int nx, int ny, int nz, double rho_void,
+                         double eta, float* __restrict__ r32, double* __restrict__ r64) {
+  const i64 nxy = (i64)nx * ny, nn = nxy * nz;
+  const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / nxy);
+  const int i1 = i + 1 == nx ? 0 : i + 1, j1 = j + 1 == ny ? 0 : j + 1, k1 = k + 1 == nz ? 0 : k + 1;
+  double s = 0.0;
+  const int xs[2] = {i, i1}, ys[2] = {j, j1}, zs[2] = {k, k1};
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    s += (double)phi[xs[c & 1] + nx * (ys[(c >> 1) & 1] + (i64)ny * zs[c >> 2])];
+  s *= 0.125;
+  double H;
+  if (s < -eta) H = 0.0;
+  else if (s > eta) H = 1.0;
+  else {
+    const double t = s / eta;
+    H = 0.5 * (1.0 + t + sin(M_PI * t) / M_PI);
+  }
+  const double r = 1.0 - (1.0 - rho_void) * H;
+  r64[e] = r;
+  r32[e] = (float)r;
+}
+
+template <typename Tin>
+__global__ void k_rho_copy(const Tin* __restrict__ in, i64 n, float* __restrict__ r32,
+                           double* __restrict__ r64, int* bad) {
+  const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const double r = (double)in[e];
+  if (!(r > 0.0) || !isfinite(r)) atomicAdd(bad, 1);
+  r64[e] = r;
+  r32[e] = (float)r;
+}
+
+// bhat^I_c(n) = -sgn_c sum_{e around n} rho_e F[4 a_e + c][I]; sgn = -1 for phi.
+__global__ void __launch_bounds__(kB)
+k_rhs9(const double* __restrict__ rho, const __grid_constant__ RhsParams P, int mask,
+       double* __restrict__ b, int nx, int ny, int nz) {
+  const i64 nxy = (i64)nx * ny, nn = nxy * nz;
+  const i64 n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / nxy);
+  double acc[4][9];
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int I = 0; I < 9; ++I) acc[c][I] = 0.0;
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+    const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+    const int ei = ex ? i : (i == 0 ? nx - 1 : i - 1);
+    const int ej = ey ? j : (j == 0 ? ny - 1 : j - 1);
+    const int ek = ez ? k : (k == 0 ? nz - 1 : k - 1);
+    const double r = rho[ei + nx * (ej + (i64)ny * ek)];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int I = 0; I < 9; ++I) acc[c][I] = fma(r, P.F[(4 * la + c) * 9 + I], acc[c][I]);
+  }
+#pragma unroll
+  for (int I = 0; I < 9; ++I)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double v = ((mask >> I) & 1) ? (c == 3 ? acc[c][I] : -acc[c][I]) : 0.0;
+      b[((i64)I * 4 + c) * nn + n] = v;
+    }
+}
+
+// grid (nblk, nrhs*4): partial sums of each (rhs, comp) plane.
+__global__ void __launch_bounds__(kB)
+k_comp_sums(const double* __restrict__ x, i64 nn, double* __restrict__ partial) {
+  __shared__ double sh[kWarps];
+  const int qc = blockIdx.y;
+  const i64 chunk = (nn + gridDim.x - 1) / gridDim.x;
+  const i64 lo = (i64)blockIdx.x * chunk, hi = lo + chunk < nn ? lo + chunk : nn;
+  const double* X = x + (i64)qc * nn;
+  double s = 0.0;
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += X[k];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[(i64)qc * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_sub_means(double* __restrict__ x, i64 nn, const double* __restrict__ sums) {
+  const int qc = blockIdx.y;
+  const double m = sums[qc] / (double)nn;
+  double* X = x + (i64)qc * nn;
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += (i64)gridDim.x * blockDim.x)
+    X[k] -= m;
+}
+
+// grid (nblk, 9): row I of sum_c sgn_c <u^I_c, v^J_c>, J = 0..8.
+__global__ void __launch_bounds__(kB)
+k_gram9(const double* __restrict__ u, const double* __restrict__ v, i64 nn,
+        double* __restrict__ partial) {
+  __shared__ double sh[kWarps];
+  const int I = blockIdx.y;
+  const i64 len = 4 * nn;
+  const i64 chunk = (len + gridDim.x - 1) / gridDim.x;
+  const i64 lo = (i64)blockIdx.x * chunk, hi = lo + chunk < len ? lo + chunk : len;
+  const double* U = u + (i64)I * len;
+  double acc[9];
+#pragma unroll
+  for (int J = 0; J < 9; ++J) acc[J] = 0.0;
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
+    const double sg = (k >= 3 * nn) ? -1.0 : 1.0;
+    const double uk = sg * U[k];
+#pragma unroll
+    for (int J = 0; J < 9; ++J) acc[J] = fma(uk, v[(i64)J * len + k], acc[J]);
+  }
+  for (int J = 0; J < 9; ++J) {
+    const double s = block_sum(acc[J], sh);
+    if (threadIdx.x == 0) partial[((i64)I * gridDim.x + blockIdx.x) * 9 + J] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kB)
+k_sum(const double* __restrict__ x, i64 n, double* __restrict__ partial) {
+  __shared__ double sh[kWarps];
+  const i64 chunk = (n + gridDim.x - 1) / gridDim.x;
+  const i64 lo = (i64)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
+  double s = 0.0;
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += x[k];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// One warp per element; lane a owns local dof a = 4*node + comp.
+// g_e = sum_J (K0 W^J)_a (sum_I G_IJ W^I_a) summed over lanes.
+template <typename T>
+__global__ void __launch_bounds__(kB)
+k_sens(const double* __restrict__ y, const double* __restrict__ rho, const double* __restrict__ K0,
+       const __grid_constant__ SensParams P, T* __restrict__ g, int nx, int ny, int nz,
+       int times_rho) {
+  __shared__ T Ks[32][33];
+  for (int t = threadIdx.x; t < 1024; t += kB) Ks[t / 32][t % 32] = (T)K0[t];
+  __syncthreads();
+  const i64 nxy = (i64)nx * ny, nn = nxy * nz;
+  const i64 e = (i64)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (e >= nn) return;
+  const int lane = threadIdx.x & 31;
+  const int ln = lane >> 2, comp = lane & 3;
+  const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / nxy);
+  const int ni = (i + (ln & 1)) % nx, nj = (j + ((ln >> 1) & 1)) % ny, nk = (k + (ln >> 2)) % nz;
+  const i64 node = ni + nx * (nj + (i64)ny * nk);
+  T W[9];
+#pragma unroll
+  for (int J = 0; J < 9; ++J) W[J] = (T)(P.Z[lane * 9 + J] + y[((i64)J * 4 + comp) * nn + node]);
+  T U[9];
+#pragma unroll
+  for (int J = 0; J < 9; ++J) U[J] = T(0);
+#pragma unroll 4
+  for (int b = 0; b < 32; ++b) {
+    const T kab = Ks[lane][b];
+#pragma unroll
+    for (int J = 0; J < 9; ++J) U[J] = fma(kab, __shfl_sync(0xffffffffu, W[J], b), U[J]);
+  }
+  T part = T(0);
+#pragma unroll
+  for (int J = 0; J < 9; ++J) {
+    T vj = T(0);
+#pragma unroll
+    for (int I = 0; I < 9; ++I) vj = fma((T)P.G[I * 9 + J], W[I], vj);
+    part = fma(U[J], vj, part);
+  }
+  double tot = warp_sum((double)part);
+  if (lane == 0) g[e] = (T)(times_rho ? tot * rho[e] : tot);
+}
+
+inline unsigned nb(i64 n) { return (unsigned)((n + kB - 1) / kB); }
+
+}  // namespace
+
+template <typename Tin>
+void ersatz(const Tin* phi, int nx, int ny, int nz, double rho_void, double eta, float* rho32,
+            double* rho64, cudaStream_t s) {
+  const i64 nn = (i64)nx * ny * nz;
+  k_ersatz<Tin><<<nb(nn), kB, 0, s>>>(phi, nx, ny, nz, rho_void, eta, rho32, rho64);
+}
+
+template <typename Tin>
+void rho_copy(const Tin* in, i64 n, float* rho32, double* rho64, int* bad, cudaStream_t s) {
+  k_rho_copy<Tin><<<nb(n), kB, 0, s>>>(in, n, rho32, rho64, bad);
+}
+
+void rhs9(const double* rho, const RhsParams& F, int mask, double* b, int nx, int ny, int nz,
+          cudaStream_t s) {
+  const i64 nn = (i64)nx * ny * nz;
+  k_rhs9<<<nb(nn), kB, 0, s>>>(rho, F, mask, b, nx, ny, nz);
+}
+
+void comp_sums(const double* x, i64 nn, int nrhs, double* partial, int nblk, double* out,
+               cudaStream_t s) {
+  k_comp_sums<<<dim3(nblk, nrhs * 4), kB, 0, s>>>(x, nn, partial);
+  reduce_partials(partial, nblk, 1, 1, out, 0, nrhs * 4, nullptr, s);
+}
+
+void sub_means(double* x, i64 nn, int nrhs, const double* sums, cudaStream_t s) {
+  unsigned g = nb(nn);
+  if (g > 2048) g = 2048;
+  k_sub_means<<<dim3(g, nrhs * 4), kB, 0, s>>>(x, nn, sums);
+}
+
+void gram9(const double* u, const double* v, i64 nn, double* partial, int nblk, double* out,
+           cudaStream_t s) {
+  k_gram9<<<dim3(nblk, 9), kB, 0, s>>>(u, v, nn, partial);
+  reduce_partials(partial, nblk, 9, 9, out, 0, 9, nullptr, s);
+}
+
+void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s) {
+  k_sum<<<nblk, kB, 0, s>>>(x, n, partial);
+  reduce_partials(partial, nblk, 1, 1, out, 0, 1, nullptr, s);
+}
+
+template <typename T>
+void sensitivity(const double* y, const double* rho, const double* K0dev, const SensParams& P, T* g,
+                 int nx, int ny, int nz, int times_rho, cudaStream_t s) {
+  const i64 nn = (i64)nx * ny * nz;
+  k_sens<T><<<(unsigned)((nn + kWarps - 1) / kWarps), kB, 0, s>>>(y, rho, K0dev, P, g, nx, ny, nz,
+                                                                  times_rho);
+}
+
+template void ersatz<float>(const float*, int, int, int, double, double, float*, double*, cudaStream_t);
+template void ersatz<double>(const double*, int, int, int, double, double, float*, double*, cudaStream_t);
+template void rho_copy<float>(const float*, i64, float*, double*, int*, cudaStream_t);
+template void rho_copy<double>(const double*, i64, float*, double*, int*, cudaStream_t);
+template void sensitivity<float>(const double*, const double*, const double*, const SensParams&,
+                                 float*, int, int, int, int, cudaStream_t);
+template void sensitivity<double>(const double*, const double*, const double*, const SensParams&,
+                                  double*, int, int, int, int, cudaStream_t);
+
+}  // namespace cell

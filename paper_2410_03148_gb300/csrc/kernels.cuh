@@ -1,0 +1,153 @@
+// Internal declarations shared by the library's CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace cell {
+
+typedef long long i64;
+
+// Leading dimension of the per-load Krylov scalars (Gram-Schmidt columns,
+// partial sums); bounds the GMRES restart length.
+constexpr int kNvMax = 64;
+
+// Loads: F = K0 Zbar (32 x 9, row-major) for the right-hand sides.
+struct RhsParams {
+  double F[32 * 9];
+};
+
+// Sensitivity: the affine load fields Zbar (32 x 9, row-major) and the
+// upstream weights G (9 x 9, row-major) of L = sum G_IJ H_IJ.
+struct SensParams {
+  double Z[32 * 9];
+  double G[81];
+};
+
+// Fixed element matrix passed by value as a kernel parameter: (8*NCM)^2
+// entries, row-major over local dofs NCM*node + comp.  Kernel parameters live
+// in the constant bank, so fully unrolled loops read the entries as FFMA/DFMA
+// constant operands.
+template <typename T, int NCM>
+struct FixedMat {
+  T k[64 * NCM * NCM];
+};
+
+enum ApplyMode {
+  AM_LINEAR = 0,       // y = alpha*(A x) + beta*b            (b optional)
+  AM_CHEB = 1,         // x = d_old(gathered):  sol += d_old; r -= A d_old;
+                       //                       d_new = c1 d_old + c2 Dinv r
+  AM_CHEB_LAST = 2,    // sol += d_old; r -= A d_old
+  AM_RESID_CHEB0 = 3   // x = sol(gathered): r = b - A sol; d_new = c2 Dinv r
+};
+
+// Pointers of an operator application.  Every field vector is a set of nrhs
+// component-planar blocks: value(rhs q, comp c, node n) = p[q*stride + c*nn + n].
+template <typename T>
+struct ApplyArgs {
+  const T* x; i64 xs;      // gathered input
+  T* y; i64 ys;            // LINEAR: output; CHEB modes: residual (in/out)
+  const T* b; i64 bs;      // LINEAR: optional addend; RESID_CHEB0: right-hand side
+  T* sol; i64 ss;          // CHEB modes: iterate (in/out)
+  T* dout; i64 ds;         // CHEB / RESID_CHEB0: new search direction
+  const T* dinv;           // [NC][nn] inverse diagonal
+  const T* rho;            // per-element scale (fixed-matrix operators)
+  const T* ke;             // per-element matrices, SoA: ke[entry*ne + e]
+  T alpha, beta, c1, c2;
+  int nx, ny, nz;
+  int sol_zero;            // CHEB modes: incoming sol is implicitly zero
+  const int* active;       // per-rhs flag (nullptr = all active)
+};
+
+// ---- operator applies (apply.cu) -------------------------------------------
+// Full nonsymmetric operator Ahat (4 -> 4 comps, potential rows negated).
+template <typename T> void apply_full(const ApplyArgs<T>& a, const FixedMat<T, 4>& M, int mode,
+                                      int nrhs, cudaStream_t s);
+// Elastic block A (3 -> 3).
+template <typename T> void apply_uu(const ApplyArgs<T>& a, const FixedMat<T, 4>& M, int mode,
+                                    int nrhs, cudaStream_t s);
+// Coupling block B (u -> phi rows of the symmetric form), LINEAR only.
+template <typename T> void apply_pu(const ApplyArgs<T>& a, const FixedMat<T, 4>& M, int nrhs,
+                                    cudaStream_t s);
+// Local-Schur operator Sbar = sum rho_e S0 (1 -> 1).
+template <typename T> void apply_ss(const ApplyArgs<T>& a, const FixedMat<T, 1>& M, int mode,
+                                    int nrhs, cudaStream_t s);
+// Per-element-matrix operator on a coarse level (NC = 1 or 3).
+template <typename T, int NC> void apply_elem(const ApplyArgs<T>& a, int mode, int nrhs,
+                                              cudaStream_t s);
+
+// ---- multigrid helpers (mg.cu) ----------------------------------------------
+template <typename T, int NC> void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds,
+                                             const T* dinv, T c2, i64 nn, int nrhs,
+                                             const int* active, cudaStream_t s);
+template <typename T, int NC> void axpy_view(T* x, i64 xs, const T* d, i64 ds, i64 nn, int nrhs,
+                                             const int* active, cudaStream_t s);
+template <typename T, int NC> void restrict_fw(const T* rf, i64 rs, T* bc, i64 bs, int nx, int ny,
+                                               int nz, int nrhs, const int* active, cudaStream_t s);
+template <typename T, int NC> void prolong_add(const T* xc, i64 cs, T* xf, i64 fs, int nx, int ny,
+                                               int nz, int nrhs, const int* active, cudaStream_t s);
+// Galerkin coarse element matrices.  Fine level given either as fixed matrix
+// (device pointer to (8NC)^2 values) times rho, or as per-element SoA matrices.
+template <typename T, int NC> void galerkin(const T* fixedm, const T* rho, const T* kef, T* kec,
+                                            int ncx, int ncy, int ncz, cudaStream_t s);
+template <typename T, int NC> void diag_inv(const T* fixedm, const T* rho, const T* ke, T* dinv,
+                                            int nx, int ny, int nz, cudaStream_t s);
+// max over elements of lambda_max(diag(K_e)^-1 K_e) (power iteration), as the
+// float bits of a positive float in *out (atomicMax; *out must start at 0).
+template <typename T, int NC> void elem_lmax(const T* ke, i64 ne, unsigned int* out, cudaStream_t s);
+template <typename T> void dense_solve(const T* Ainv, int n, const T* b, i64 bs, T* x, i64 xs,
+                                       i64 nn, int nc, int nrhs, const int* active, cudaStream_t s);
+
+// ---- Krylov helpers (krylov.cu) ---------------------------------------------
+// partial[(q*nblk + blk)*nvmax + i] = block-partial of <V_i, w> for rhs q.
+template <typename T> void multidot(const T* V, i64 vstride, i64 rstride, int nv, const T* w,
+                                    i64 wstride, i64 len, double* partial, int nblk, int nvmax,
+                                    int nrhs, const int* active, cudaStream_t s);
+// out[q*nvmax + i] (+)= sum over blocks of partial
+void reduce_partials(const double* partial, int nblk, int nv, int nvmax, double* out, int accumulate,
+                     int nrhs, const int* active, cudaStream_t s);
+// w -= sum_i h[q*nvmax+i] V_i ; then (mode 1) partial dots <V_i,w> or (mode 2) partial |w|^2
+template <typename T> void update(const T* V, i64 vstride, i64 rstride, int nv, const double* h,
+                                  int nvmax, T* w, i64 wstride, i64 len, int mode, double* partial,
+                                  int nblk, int nrhs, const int* active, cudaStream_t s);
+template <typename T> void scale_vec(T* w, i64 wstride, i64 len, const double* sc, int nrhs,
+                                     cudaStream_t s);
+template <typename T> void lincomb(const T* V, i64 vstride, i64 rstride, const double* y,
+                                   const int* kcount, int nvmax, T* u, i64 ustride, i64 len,
+                                   int nrhs, const int* active, cudaStream_t s);
+void givens_step(double* H, double* cs, double* sn, double* g, const double* hcol,
+                 const double* hnorm2, int j, int m, int* active, double* resid, const double* tolabs,
+                 double* invscale, int* kcount, int nrhs, cudaStream_t s);
+void backsolve(const double* H, const double* g, const int* kcount, int m, double* y, int nrhs,
+               const int* mask, cudaStream_t s);
+void start_cycle(const double* beta2, double* g, int m, int* active, const int* want, double* resid,
+                 double* invscale, const double* tolabs, int* kcount, int nrhs, cudaStream_t s);
+// v32[q] = (float)(r64[q] * sc[q])   or  x64[q] += sc[q] * d32[q]
+void to_f32_scaled(const double* r, i64 rs, float* v, i64 vs, i64 len, const double* sc, int nrhs,
+                   const int* active, cudaStream_t s);
+template <typename T> void axpy_f64(double* x, i64 xs, const T* d, i64 ds, i64 len, const double* sc,
+                                    int nrhs, const int* active, cudaStream_t s);
+template <typename T> void fill(T* p, i64 n, T v, cudaStream_t s);
+
+// ---- cell-level kernels (cellk.cu) -------------------------------------------
+template <typename Tin> void ersatz(const Tin* phi, int nx, int ny, int nz, double rho_void,
+                                    double eta, float* rho32, double* rho64, cudaStream_t s);
+template <typename Tin> void rho_copy(const Tin* in, i64 n, float* rho32, double* rho64,
+                                      int* bad, cudaStream_t s);
+void rhs9(const double* rho, const RhsParams& F, int mask, double* b, int nx, int ny, int nz,
+          cudaStream_t s);
+// per-(rhs, comp) sums -> out[q*4 + c]
+void comp_sums(const double* x, i64 nn, int nrhs, double* partial, int nblk, double* out,
+               cudaStream_t s);
+void sub_means(double* x, i64 nn, int nrhs, const double* sums, cudaStream_t s);
+// G_IJ (+)= sum_n sum_c sgn_c u^I_c v^J_c, sgn = -1 for the potential component
+void gram9(const double* u, const double* v, i64 nn, double* partial, int nblk, double* out,
+           cudaStream_t s);
+// out[0] = sum of x[0..n)  (device scalar)
+void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s);
+// g_e = (rho_e if times_rho) * sum_IJ G_IJ W_e^I . K0 W_e^J, W = Zbar + y_e
+template <typename T> void sensitivity(const double* y, const double* rho, const double* K0dev,
+                                       const SensParams& P, T* g, int nx, int ny, int nz,
+                                       int times_rho, cudaStream_t s);
+
+}  // namespace cell

@@ -1,0 +1,335 @@
+// Batched GMRES building blocks (§2.5: right-preconditioned GMRES, one Krylov
+// space per load case): block-partial dot products with FP64 accumulation,
+// fused Gram-Schmidt updates, deterministic partial reductions, and the FP64
+// Hessenberg / Givens least-squares recurrences on the device.
+#include "kernels.cuh"
+
+namespace cell {
+
+namespace {
+
+constexpr int kB = 256;
+constexpr int kWarps = kB / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block reduction of one value per thread; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < kWarps ? sh[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;
+}
+
+// grid (nblk, nrhs); each block covers a contiguous chunk of len.
+template <typename T>
+__global__ void __launch_bounds__(kB)
+k_multidot(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const T* __restrict__ w,
+           i64 wstride, i64 len, double* __restrict__ partial, int nvmax, const int* active) {
+  __shared__ double sh[kWarps];
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  const i64 chunk = (len + gridDim.x - 1) / gridDim.x;
+  const i64 lo = (i64)blockIdx.x * chunk;
+  const i64 hi = lo + chunk < len ? lo + chunk : len;
+  const T* W = w + q * wstride;
+  for (int i = 0; i < nv; ++i) {
+    const T* Vi = V + i * vstride + q * rstride;
+    double s = 0.0;
+    for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += (double)Vi[k] * (double)W[k];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + i] = s;
+  }
+}
+
+// One warp per (rhs, i): fixed-order sum over blocks.
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, int nv, int nvmax,
+                                  double* __restrict__ out, int accumulate, const int* active) {
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = lane; b < nblk; b += 32) s += partial[((i64)q * nblk + b) * nvmax + i];
+  s = warp_sum(s);
+  if (lane == 0) out[q * nvmax + i] = accumulate ? out[q * nvmax + i] + s : s;
+}
+
+// w -= sum_i h_i V_i over this block's chunk, then partial dots or norm.
+template <typename T>
+__global__ void __launch_bounds__(kB)
+k_update(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const double* __restrict__ h,
+         int nvmax, T* __restrict__ w, i64 wstride, i64 len, int mode, double* __restrict__ partial,
+         const int* active) {
+  __shared__ double sh[kWarps];
+  __shared__ double hs[64];
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  for (int i = threadIdx.x; i < nv; i += kB) hs[i] = h[q * nvmax + i];
+  __syncthreads();
+  const i64 chunk = (len + gridDim.x - 1) / gridDim.x;
+  const i64 lo = (i64)blockIdx.x * chunk;
+  const i64 hi = lo + chunk < len ? lo + chunk : len;
+  T* W = w + q * wstride;
+  const T* V0 = V + q * rstride;
+  double nrm = 0.0;
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
+    double acc = (double)W[k];
+    for (int i = 0; i < nv; ++i) acc -= hs[i] * (double)V0[i * vstride + k];
+    const T v = (T)acc;
+    W[k] = v;
+    nrm += (double)v * (double)v;
+  }
+  if (mode == 2) {
+    nrm = block_sum(nrm, sh);
+    if (threadIdx.x == 0) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + 0] = nrm;
+  } else if (mode == 1) {
+    // second pass over the chunk (now cache-resident) for the reorthogonalisation dots
+    for (int i = 0; i < nv; ++i) {
+      const T* Vi = V0 + i * vstride;
+      double s = 0.0;
+      for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += (double)Vi[k] * (double)W[k];
+      s = block_sum(s, sh);
+      if (threadIdx.x == 0) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + i] = s;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scale(T* __restrict__ w, i64 wstride, i64 len, const double* __restrict__ sc) {
+  const int q = blockIdx.y;
+  const double f = sc[q];
+  if (f == 1.0) return;
+  T* W = w + q * wstride;
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x)
+    W[k] = (T)((double)W[k] * f);
+}
+
+template <typename T>
+__global__ void k_lincomb(const T* __restrict__ V, i64 vstride, i64 rstride,
+                          const double* __restrict__ y, const int* __restrict__ kcount, int nvmax,
+                          T* __restrict__ u, i64 ustride, i64 len, const int* active) {
+  __shared__ double ys[64];
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  const int kq = kcount[q];
+  for (int i = threadIdx.x; i < kq; i += blockDim.x) ys[i] = y[q * nvmax + i];
+  __syncthreads();
+  const T* V0 = V + q * rstride;
+  T* U = u + q * ustride;
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < kq; ++i) acc += ys[i] * (double)V0[i * vstride + k];
+    U[k] = (T)acc;
+  }
+}
+
+// Column j of the Hessenberg matrix: hcol[0..j] from Gram-Schmidt and
+// h_{j+1,j} = sqrt(hnorm2).  Applies the stored rotations, forms the new one,
+// updates the least-squares right-hand side g and the residual estimate.
+// H is stored per rhs column-major with leading dimension m+1.
+__global__ void k_givens(double* H, double* cs, double* sn, double* g, const double* hcol,
+                         const double* hnorm2, int j, int m, int nvmax, int* active, double* resid,
+                         const double* tolabs, double* invscale, int* kcount, int nrhs) {
+  const int q = threadIdx.x;
+  if (q >= nrhs) return;
+  if (!active[q]) {
+    invscale[q] = 1.0;
+    return;
+  }
+  double* Hq = H + (i64)q * (m + 1) * m + (i64)j * (m + 1);
+  double* cq = cs + q * m;
+  double* sq = sn + q * m;
+  double* gq = g + q * (m + 1);
+  for (int i = 0; i <= j; ++i) Hq[i] = hcol[q * nvmax + i];
+  const double hn = sqrt(fmax(hnorm2[q * nvmax], 0.0));
+  for (int i = 0; i < j; ++i) {
+    const double a = Hq[i], b = Hq[i + 1];
+    Hq[i] = cq[i] * a + sq[i] * b;
+    Hq[i + 1] = -sq[i] * a + cq[i] * b;
+  }
+  const double a = Hq[j], b = hn;
+  const double rr = hypot(a, b);
+  double c = 1.0, s = 0.0;
+  if (rr > 0.0) {
+    c = a / rr;
+    s = b / rr;
+  }
+  cq[j] = c;
+  sq[j] = s;
+  Hq[j] = rr;
+  Hq[j + 1] = 0.0;
+  const double gj = gq[j];
+  gq[j] = c * gj;
+  gq[j + 1] = -s * gj;
+  const double res = fabs(gq[j + 1]);
+  resid[q] = res;
+  kcount[q] = j + 1;
+  // breakdown (invariant subspace) or convergence: this space is done
+  const bool brk = !(hn > 1e-300) || !(hn > 1e-14 * fabs(rr));
+  invscale[q] = brk ? 0.0 : 1.0 / hn;
+  if (res <= tolabs[q] || brk || j + 1 >= m) active[q] = 0;
+}
+
+// Solve the k x k upper-triangular R y = g per rhs (mask: rhs that ran this cycle).
+__global__ void k_backsolve(const double* H, const double* g, const int* kcount, int m, double* y,
+                            int nvmax, int nrhs, const int* mask) {
+  const int q = threadIdx.x;
+  if (q >= nrhs || !mask[q]) return;
+  const int k = kcount[q];
+  const double* Hq = H + (i64)q * (m + 1) * m;
+  const double* gq = g + q * (m + 1);
+  double* yq = y + q * nvmax;
+  for (int i = k - 1; i >= 0; --i) {
+    double t = gq[i];
+    for (int l = i + 1; l < k; ++l) t -= Hq[(i64)l * (m + 1) + i] * yq[l];
+    const double d = Hq[(i64)i * (m + 1) + i];
+    yq[i] = d != 0.0 ? t / d : 0.0;
+  }
+}
+
+// Start of a GMRES cycle: beta = ||r0||, g = beta e1, v0 scale = 1/beta.
+__global__ void k_start_cycle(const double* beta2, double* g, int m, int nvmax, int* active,
+                              const int* want, double* resid, double* invscale,
+                              const double* tolabs, int* kcount, int nrhs) {
+  const int q = threadIdx.x;
+  if (q >= nrhs) return;
+  const double beta = sqrt(fmax(beta2[q * nvmax], 0.0));
+  double* gq = g + q * (m + 1);
+  for (int i = 0; i <= m; ++i) gq[i] = 0.0;
+  gq[0] = beta;
+  resid[q] = beta;
+  kcount[q] = 0;
+  const bool go = want[q] && beta > tolabs[q] && beta > 0.0;
+  active[q] = go ? 1 : 0;
+  invscale[q] = go ? 1.0 / beta : 1.0;
+}
+
+__global__ void k_to_f32(const double* __restrict__ r, i64 rs, float* __restrict__ v, i64 vs,
+                         i64 len, const double* __restrict__ sc, const int* active) {
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  const double f = sc[q];
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x)
+    v[q * vs + k] = (float)(r[q * rs + k] * f);
+}
+
+template <typename T>
+__global__ void k_axpy_f64(double* __restrict__ x, i64 xs, const T* __restrict__ d, i64 ds, i64 len,
+                           const double* __restrict__ sc, const int* active) {
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  const double f = sc[q];
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x)
+    x[q * xs + k] += f * (double)d[q * ds + k];
+}
+
+template <typename T>
+__global__ void k_fill(T* p, i64 n, T v) {
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (i64)gridDim.x * blockDim.x) p[k] = v;
+}
+
+inline unsigned stream_blocks(i64 len) {
+  i64 b = (len + kB - 1) / kB;
+  if (b > 4096) b = 4096;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+template <typename T>
+void multidot(const T* V, i64 vstride, i64 rstride, int nv, const T* w, i64 wstride, i64 len,
+              double* partial, int nblk, int nvmax, int nrhs, const int* active, cudaStream_t s) {
+  k_multidot<T><<<dim3(nblk, nrhs), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride, len, partial,
+                                                 nvmax, active);
+}
+
+void reduce_partials(const double* partial, int nblk, int nv, int nvmax, double* out, int accumulate,
+                     int nrhs, const int* active, cudaStream_t s) {
+  const int wpb = 4;
+  k_reduce_partials<<<dim3((nv + wpb - 1) / wpb, nrhs), 32 * wpb, 0, s>>>(partial, nblk, nv, nvmax,
+                                                                         out, accumulate, active);
+}
+
+template <typename T>
+void update(const T* V, i64 vstride, i64 rstride, int nv, const double* h, int nvmax, T* w,
+            i64 wstride, i64 len, int mode, double* partial, int nblk, int nrhs, const int* active,
+            cudaStream_t s) {
+  k_update<T><<<dim3(nblk, nrhs), kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len,
+                                               mode, partial, active);
+}
+
+template <typename T>
+void scale_vec(T* w, i64 wstride, i64 len, const double* sc, int nrhs, cudaStream_t s) {
+  k_scale<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(w, wstride, len, sc);
+}
+
+template <typename T>
+void lincomb(const T* V, i64 vstride, i64 rstride, const double* y, const int* kcount, int nvmax,
+             T* u, i64 ustride, i64 len, int nrhs, const int* active, cudaStream_t s) {
+  k_lincomb<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(V, vstride, rstride, y, kcount, nvmax,
+                                                              u, ustride, len, active);
+}
+
+void givens_step(double* H, double* cs, double* sn, double* g, const double* hcol,
+                 const double* hnorm2, int j, int m, int* active, double* resid,
+                 const double* tolabs, double* invscale, int* kcount, int nrhs, cudaStream_t s) {
+  k_givens<<<1, 32, 0, s>>>(H, cs, sn, g, hcol, hnorm2, j, m, 64, active, resid, tolabs, invscale,
+                            kcount, nrhs);
+}
+
+void backsolve(const double* H, const double* g, const int* kcount, int m, double* y, int nrhs,
+               const int* mask, cudaStream_t s) {
+  k_backsolve<<<1, 32, 0, s>>>(H, g, kcount, m, y, 64, nrhs, mask);
+}
+
+void start_cycle(const double* beta2, double* g, int m, int* active, const int* want, double* resid,
+                 double* invscale, const double* tolabs, int* kcount, int nrhs, cudaStream_t s) {
+  k_start_cycle<<<1, 32, 0, s>>>(beta2, g, m, 64, active, want, resid, invscale, tolabs, kcount, nrhs);
+}
+
+void to_f32_scaled(const double* r, i64 rs, float* v, i64 vs, i64 len, const double* sc, int nrhs,
+                   const int* active, cudaStream_t s) {
+  k_to_f32<<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(r, rs, v, vs, len, sc, active);
+}
+
+template <typename T>
+void axpy_f64(double* x, i64 xs, const T* d, i64 ds, i64 len, const double* sc, int nrhs,
+              const int* active, cudaStream_t s) {
+  k_axpy_f64<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(x, xs, d, ds, len, sc, active);
+}
+
+template <typename T>
+void fill(T* p, i64 n, T v, cudaStream_t s) {
+  k_fill<T><<<stream_blocks(n), kB, 0, s>>>(p, n, v);
+}
+
+#define INST(T)                                                                                    \
+  template void multidot<T>(const T*, i64, i64, int, const T*, i64, i64, double*, int, int, int,   \
+                            const int*, cudaStream_t);                                             \
+  template void update<T>(const T*, i64, i64, int, const double*, int, T*, i64, i64, int, double*, \
+                          int, int, const int*, cudaStream_t);                                     \
+  template void scale_vec<T>(T*, i64, i64, const double*, int, cudaStream_t);                      \
+  template void lincomb<T>(const T*, i64, i64, const double*, const int*, int, T*, i64, i64, int,  \
+                           const int*, cudaStream_t);                                              \
+  template void axpy_f64<T>(double*, i64, const T*, i64, i64, const double*, int, const int*,      \
+                            cudaStream_t);                                                         \
+  template void fill<T>(T*, i64, T, cudaStream_t);
+INST(float)
+INST(double)
+template void fill<int>(int*, i64, int, cudaStream_t);
+#undef INST
+
+}  // namespace cell

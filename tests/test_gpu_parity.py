@@ -1,0 +1,229 @@
+"""GPU parity of the CUDA path against the FP64 CPU oracle, through the C ABI.
+
+Tolerances: FP64 kernels (apply, right-hand sides, ersatz) agree with the
+oracle to rounding (1e-12 relative); FP32 kernels to 2e-6 relative (a few
+FP32 ulps accumulated over 8 elements x 32 terms); homogenised tensors of a
+solve to tol = 1e-10 agree to 1e-8 relative per block (FP64 path and mixed
+path alike: the energy form's error is quadratic in the solve error and the
+refinement residual is FP64).
+"""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import cellgen
+from oracle import ersatz, fem, laminate, sensitivity
+
+pytestmark = pytest.mark.gpu
+
+MAT = cellgen.pzt5h_class()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2410_03148_gb300 import load
+    return load()
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def to_dof(xc):
+    """(nrhs, 4, nz, ny, nx) cell vectors -> (4N, nrhs) oracle dof order."""
+    xc = np.asarray(xc)
+    nr = xc.shape[0]
+    return xc.reshape(nr, 4, -1).transpose(2, 1, 0).reshape(-1, nr)
+
+
+def from_dof(xd, shape):
+    nr = xd.shape[1]
+    return xd.reshape(-1, 4, nr).transpose(2, 1, 0).reshape((nr, 4) + tuple(shape))
+
+
+def negate_phi_rows(yd):
+    yd = yd.copy()
+    yd[3::4] *= -1
+    return yd
+
+
+def block_errors(Ch, eh, kh, ref):
+    return (np.abs(Ch - ref["C"]).max() / np.abs(ref["C"]).max(),
+            np.abs(eh - ref["e"]).max() / np.abs(ref["e"]).max(),
+            np.abs(kh - ref["kappa"]).max() / np.abs(ref["kappa"]).max())
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_levelset(shape, seed):
+    phi = cellgen.gaussian_levelset(shape, seed=seed)
+    rho = ersatz.rho_from_levelset(phi)
+    return phi, fem.solve_cell(rho, *MAT)
+
+
+def make_cell(design, kind, **opt):
+    from paper_2410_03148_gb300 import Cell
+    return Cell(torch.as_tensor(np.ascontiguousarray(design), device=dev()), MAT, kind=kind, **opt)
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 6, 7), (16, 16, 16), (2, 3, 2)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_apply_matches_oracle_matvec(shape, dtype):
+    rho = cellgen.random_rho(shape, seed=1)
+    cell = make_cell(rho, "rho")
+    P = fem.CellProblem(rho, *MAT)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((3, 4) + shape)
+    y = cell.apply(torch.as_tensor(x, device=dev(), dtype=dtype)).double().cpu().numpy()
+    yref = from_dof(negate_phi_rows(P.Kg @ to_dof(x)), shape)
+    tol = 1e-12 if dtype == torch.float64 else 2e-6
+    scale = np.abs(P.Kg).max() * np.abs(x).max() * 8
+    assert np.abs(y - yref).max() < tol * scale
+
+
+def test_rhs_and_rho_match_oracle():
+    shape = (6, 5, 4)
+    phi = cellgen.gaussian_levelset(shape, seed=3)
+    cell = make_cell(phi, "phi")
+    rho_ref = ersatz.rho_from_levelset(phi)
+    rho = cell.rho().cpu().numpy()
+    assert np.abs(rho - rho_ref).max() < 1e-14
+    P = fem.CellProblem(rho_ref, *MAT)
+    bref = from_dof(negate_phi_rows(P.rhs()), shape)
+    b = cell.rhs().cpu().numpy()
+    assert np.abs(b - bref).max() < 1e-13 * np.abs(bref).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("shape", [(4, 4, 4), (6, 5, 4), (8, 8, 8), (16, 16, 16)])
+def test_solve_matches_oracle(shape, precision):
+    phi, ref = oracle_levelset(shape, 0)
+    cell = make_cell(phi, "phi", precision=precision)
+    st = cell.solve()
+    assert max(st["rel_residual"]) <= 1e-10
+    errs = block_errors(*cell.homogenise(), ref)
+    assert max(errs) < 1e-8, (errs, st)
+    # solutions themselves (null space projected on both sides)
+    y = cell.solution().cpu().numpy()
+    yref = from_dof(ref["y"], shape)
+    assert np.abs(y - yref).max() < 1e-6 * np.abs(yref).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solid_and_uniform_cells(precision):
+    for val in (1.0, 0.25):
+        rho = np.full((8, 8, 8), val)
+        cell = make_cell(rho, "rho", precision=precision)
+        cell.solve()
+        Ch, eh, kh = cell.homogenise()
+        C, e, k = MAT
+        assert np.abs(Ch - val * C).max() < 1e-12 * np.abs(C).max()
+        assert np.abs(eh - val * e).max() < 1e-12 * np.abs(e).max()
+        assert np.abs(kh - val * k).max() < 1e-12 * np.abs(k).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("n,axis", [(32, 2), (32, 0), (64, 1)])
+def test_laminate_closed_form_any_size(n, axis, precision):
+    shape = (n, n, n)
+    rho = cellgen.laminate_rho(shape, axis, seed=7 + axis)
+    layers = {0: rho[0, 0, :], 1: rho[0, :, 0], 2: rho[:, 0, 0]}[axis]
+    cell = make_cell(rho, "rho", precision=precision)
+    cell.solve()
+    Ch, eh, kh = cell.homogenise()
+    Cr, er, kr, _ = laminate.laminate_tensors(*MAT, layers, axis)
+    errs = block_errors(Ch, eh, kh, {"C": Cr, "e": er, "kappa": kr})
+    assert max(errs) < 1e-8, errs
+
+
+def test_homogenised_tensors_symmetric_spd_64():
+    phi = cellgen.gaussian_levelset(64, seed=1)
+    cell = make_cell(phi, "phi")
+    st = cell.solve()
+    Ch, eh, kh = cell.homogenise()
+    assert max(st["rel_residual"]) <= 1e-10
+    assert np.linalg.eigvalsh(Ch).min() > 0 and np.linalg.eigvalsh(kh).min() > 0
+    assert np.abs(Ch - Ch.T).max() <= 1e-12 * np.abs(Ch).max()
+
+
+def test_fp64_and_mixed_paths_agree_64():
+    phi = cellgen.gaussian_levelset(64, seed=2)
+    out = []
+    for p in (0, 1):
+        cell = make_cell(phi, "phi", precision=p)
+        cell.solve()
+        out.append(cell.homogenise())
+        cell.close()
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() < 1e-8 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("gdtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("shape", [(8, 8, 8), (6, 5, 4)])
+def test_sensitivity_matches_oracle(shape, gdtype):
+    phi, ref = oracle_levelset(shape, 0)
+    cell = make_cell(phi, "phi", precision=0)
+    cell.solve()
+    rng = np.random.default_rng(5)
+    dC, de, dk = rng.standard_normal((6, 6)), rng.standard_normal((3, 6)), rng.standard_normal((3, 3))
+    g = cell.sensitivity(dC, de, dk, dtype=gdtype).double().cpu().numpy()
+    P = ref["problem"]
+    G = sensitivity.G_from_si(dC, de, dk, P.sc)
+    gref = sensitivity.grad_rho(P, ref["y"], G)
+    tol = 1e-9 if gdtype == torch.float64 else 1e-5
+    assert np.abs(g - gref).max() < tol * np.abs(gref).max()
+
+
+def test_dh_chain_matches_oracle_gradient():
+    from paper_2410_03148_gb300 import dh
+    from oracle import figures
+    shape = (8, 8, 8)
+    phi, ref = oracle_levelset(shape, 0)
+    cell = make_cell(phi, "phi")
+    cell.solve()
+    Ch, eh, kh = cell.homogenise()
+    d, dC, de = dh(Ch, eh)
+    assert abs(d - figures.d_h(ref["C"], ref["e"])) < 1e-8 * abs(d)
+    g = cell.sensitivity(dC, de, None).cpu().numpy()
+    P = ref["problem"]
+    rC, re_ = figures.d_h_grad(ref["C"], ref["e"])
+    gref = sensitivity.grad_rho(P, ref["y"], sensitivity.G_from_si(rC, re_, np.zeros((3, 3)), P.sc))
+    assert np.abs(g - gref).max() < 1e-7 * np.abs(gref).max()
+
+
+def test_autograd_backward_is_sensitivity():
+    from paper_2410_03148_gb300 import homogenise
+    rho = torch.as_tensor(cellgen.random_rho((8, 8, 8), seed=3, lo=0.05), device=dev()).requires_grad_()
+    Ch, eh, kh = homogenise(rho, MAT)
+    loss = Ch[2, 2] / 1e10 + eh[2, 2] + kh[0, 0] * 1e8
+    loss.backward()
+    P = fem.CellProblem(rho.detach().cpu().numpy(), *MAT)
+    y = P.solve()
+    dC = np.zeros((6, 6)); dC[2, 2] = 1e-10
+    de = np.zeros((3, 6)); de[2, 2] = 1.0
+    dk = np.zeros((3, 3)); dk[0, 0] = 1e8
+    gref = sensitivity.grad_rho(P, y, sensitivity.G_from_si(dC, de, dk, P.sc))
+    g = rho.grad.cpu().numpy()
+    assert np.abs(g - gref).max() < 1e-8 * np.abs(gref).max()
+
+
+def test_bitwise_reproducible():
+    phi = cellgen.gaussian_levelset(16, seed=4)
+    res = []
+    for _ in range(2):
+        cell = make_cell(phi, "phi")
+        cell.solve()
+        res.append(np.concatenate([a.ravel() for a in cell.homogenise()]))
+        cell.close()
+    assert np.array_equal(res[0], res[1])
+
+
+def test_nonpositive_rho_is_rejected():
+    from paper_2410_03148_gb300._binding import CellError
+    rho = np.ones((4, 4, 4))
+    rho[1, 2, 3] = -0.5
+    with pytest.raises(CellError):
+        make_cell(rho, "rho")
