@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark of the periodic piezoelectric cell solve on GB300.
+
+One step = the whole hot path for one design: set-up from a nodal level set
+on the device (ersatz rho, K0, S0, multigrid hierarchies), the nine
+right-hand sides, SCP-GMRES to a relative residual of 1e-10 (FP32 Krylov and
+multigrid inside FP64 restarts), null-space projection, the homogenised C^H,
+e^H, kappa^H (FP64 energy form; 1e-8 relative error against the FP64
+reference is the accuracy target) and the element sensitivities of d_h.
+
+Workload: a 64^3 unit cell (1,048,576 dof, 9 loads), PZT-5H-class base
+material, seeded level sets (sum of 8 periodic Gaussians).  The step's
+working set (about 1.5 GB: Krylov basis, multigrid levels, FP64 vectors) is
+far larger than the 129 MB L2, and a 256 MB buffer is also rewritten between
+timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one rank per GPU): independent designs per rank
+(replicas, no collective on the data path); value = total time / total cells.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "cell-solve time to C^H at 1e-8 rel err; DOF·RHS/s per apply vs HBM roofline"
+UNIT = "ms per 64^3 cell solve (9 loads, setup+solve+C^H+d_h sensitivities)"
+
+# Algorithmic cost per (node, load) of each timed kernel class of the library:
+# (flops, bytes, bound, dtype).  Bytes count one read of every input and one
+# write of every output (see the design doc for the derivation).
+CLASS_COST = {
+    "full32": (2 * (1024 + 32), 4 * 4 + 4 * 4 + 4 / 9, "alu", "f32"),
+    "full64": (2 * (1024 + 32), 8 * 4 + 8 * 4 + 8 + 8 / 9, "alu", "f64"),
+    "elastic0": (2 * (576 + 24), 4 * (3 + 2 * 3 + 2 * 3 + 3) + 4 * 3 / 9 + 4 / 9, "alu", "f32"),
+    "schur0": (2 * (64 + 8), 4 * (1 + 2 + 2 + 1) + 4 / 9 + 4 / 9, "hbm", "f32"),
+    "coupling": (2 * (192 + 8), 4 * (3 + 1 + 1) + 4 / 9, "alu", "f32"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=64)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        loaded = [s for s in sm if s > 500] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_step(n, seed):
+    """The FP64 CPU oracle on one n^3 design: ersatz, assembly, direct solve,
+    energy-form homogenisation and the d_h element sensitivities."""
+    import cellgen
+    from oracle import ersatz, fem, figures, sensitivity
+    mat = cellgen.pzt5h_class()
+    phi = cellgen.gaussian_levelset(n, seed=seed)
+    rho = ersatz.rho_from_levelset(phi)
+    P = fem.CellProblem(rho, *mat)
+    y = P.solve()
+    H, _ = P.homogenise(y)
+    Ch, eh, kh = P.tensors(H)
+    dC, de = figures.d_h_grad(Ch, eh)
+    sensitivity.grad_rho(P, y, sensitivity.G_from_si(dC, de, 0 * kh, P.sc))
+    return Ch
+
+
+def cpu_sample(n_target, sample_n=16, reps=1, seed0=0):
+    t = []
+    for r in range(reps):
+        t0 = time.perf_counter()
+        oracle_step(sample_n, seed0 + r)
+        t.append(time.perf_counter() - t0)
+    per = min(t)
+    scale = (n_target / sample_n) ** 3
+    return per, per * scale * 1e3
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sample_n = 16 if args.steps + args.warmup <= 12 else 12
+    for w in range(args.warmup):
+        oracle_step(sample_n, 100 + w)
+    times = []
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_step(sample_n, k)
+        times.append(time.perf_counter() - t0)
+    scale = (args.n / sample_n) ** 3
+    ms = statistics.mean(times) * 1e3 * scale
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.n}^3 periodic piezoelectric cell, 9 loads, seeded "
+                                "Gaussian level sets, PZT-5H-class",
+                   "l2": "working set > L2"},
+        "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"one {sample_n}^3 cell per step (SuperLU direct solve, single "
+                                   f"thread), time scaled by the dof ratio {scale:.0f}"},
+        "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import cellgen
+    from paper_2410_03148_gb300 import Cell, dh, load
+    from paper_2410_03148_gb300 import _binding as B
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    load()
+    mat = cellgen.pzt5h_class()
+    n = args.n
+    prec = 1 if args.precision == "mixed" else 0
+    ndes = 8
+    designs = [torch.as_tensor(cellgen.gaussian_levelset(n, seed=rank * 1000 + s), device=dev)
+               for s in range(ndes)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def step(phi, profile=0):
+        cell = Cell(phi, mat, kind="phi", precision=prec, profile=profile)
+        st = cell.solve()
+        Ch, eh, kh = cell.homogenise()
+        d, dC, de = dh(Ch, eh)
+        g = cell.sensitivity(dC, de, None, dtype=torch.float32)
+        cell.close()
+        return st, (Ch, eh, kh), g
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+
+    for w in range(args.warmup):
+        step(designs[w % ndes])
+    barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    stats = []
+    step_ms = []
+    launches0 = B.cell_launch_count()
+    stream = torch.cuda.current_stream(dev)
+    t_start = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st, _, _ = step(designs[k % ndes], profile=1)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        stats.append(st)
+    barrier()
+    wall = time.perf_counter() - t_start
+    launches = B.cell_launch_count() - launches0
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_cell = total_ms / (args.steps * world)
+
+    # roofline of the dominant kernel class, from the live CUDA events
+    hbm, hbm_kind, sm_max = peaks()
+    tot = {c: sum(s["class_ms"][c] for s in stats) for c in B.PROF_CLASSES}
+    cnt = {c: sum(s["class_count"][c] for s in stats) for c in B.PROF_CLASSES}
+    units = {c: sum(s["class_units"][c] for s in stats) for c in B.PROF_CLASSES}
+    dom = max((c for c in CLASS_COST), key=lambda c: tot[c])
+    flops_u, bytes_u, bound, kdt = CLASS_COST[dom]
+    nn = n ** 3
+    avg_ms = tot[dom] / max(cnt[dom], 1)
+    per_launch_units = units[dom] / max(cnt[dom], 1)
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12          # TFLOP/s, FP32 FMA lanes
+    fp64_peak = 1.25 * sm_max / 2070.0                        # TFLOP/s, nominal FP64 rate
+    if bound == "hbm":
+        achieved = bytes_u * nn * per_launch_units / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None}
+    else:
+        achieved = flops_u * nn * per_launch_units / (avg_ms * 1e-3) / 1e12
+        peak = fp32_peak if kdt == "f32" else fp64_peak
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None}
+    roof.update({"kernel": dom, "peak_source": f"{'hbm ' + hbm_kind if bound == 'hbm' else 'unit counts x max SM clock'}",
+                 "launches": cnt[dom], "avg_launch_ms": avg_ms,
+                 "dof_rhs_per_s": 4 * nn * per_launch_units / (avg_ms * 1e-3),
+                 "dof_rhs_per_s_hbm_roofline": hbm * 1e9 / (bytes_u / 4)})
+    class_share = {c: round(tot[c] / max(total_ms / world, 1e-9), 4) for c in B.PROF_CLASSES}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.as_tensor(cellgen.gaussian_levelset(n, seed=rank * 1000 + 500 + s)).pin_memory()
+                for s in range(2)]
+        e2e_ms = []
+        for k in range(max(2, min(args.steps, 4))):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            phi = host[k % 2].to(dev, non_blocking=True)
+            _, tens, g = step(phi)
+            g_host = g.cpu()
+            _ = [np.asarray(t) for t in tens]
+            torch.cuda.synchronize()
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+        e2e = {"value": statistics.mean(e2e_ms), "unit": UNIT,
+               "h2d_bytes_per_step": nn * 8, "d2h_bytes_per_step": nn * 4 + (36 + 18 + 9) * 8}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        per, scaled = cpu_sample(n, sample_n=16, reps=1)
+        cpu = {"value": scaled, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one 16^3 cell through the FP64 oracle ({per:.1f} s; SuperLU single "
+                         f"thread), scaled by the dof ratio {(n / 16) ** 3:.0f}"}
+
+    if rank == 0:
+        iters = [max(s["iters"]) for s in stats]
+        line = {
+            "metric": METRIC, "value": ms_per_cell, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
+            "config": {"workload": f"{n}^3 periodic piezoelectric cell ({4 * nn} dof), 9 loads, "
+                                   "seeded Gaussian level sets, PZT-5H-class, tol 1e-10",
+                       "precision": args.precision, "parallelism": f"replicas x{world}",
+                       "l2": "working set ~1.5 GB > L2, plus a 256 MB flush between steps"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "detail": {"wall_s": wall, "step_ms": step_ms, "gmres_iters_max": iters,
+                       "refinements": [s["refinements"] for s in stats],
+                       "class_ms_per_step": {c: tot[c] / args.steps for c in B.PROF_CLASSES},
+                       "class_share": class_share},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

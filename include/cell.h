@@ -89,7 +89,7 @@ typedef struct cell_options {
                           Sbar = sum_e C_e + B_e A_e^-1 B_e^T (§2.5.3, 1e-10) */
   int coarse_dofs;     /* stop coarsening once a level has at most this many dofs */
   int load_mask;       /* bit I set = solve load I (default 0x1FF = all nine) */
-  int profile;         /* nonzero: time the operator-apply kernels with CUDA events */
+  int profile;         /* nonzero: time kernel classes with CUDA events (cell_stats) */
 } cell_options;
 
 typedef struct cell_desc {
@@ -107,17 +107,29 @@ typedef struct cell_desc {
   void* stream;        /* cudaStream_t */
 } cell_desc;
 
+/* Kernel classes timed with CUDA events when cell_options.profile is set. */
+typedef enum cell_prof_class {
+  CELL_PROF_FULL32 = 0,    /* full operator Ahat, FP32 (GMRES) */
+  CELL_PROF_FULL64 = 1,    /* full operator Ahat, FP64 (refinement residual) */
+  CELL_PROF_ELASTIC0 = 2,  /* elastic block A on the fine grid (smoothing, residuals) */
+  CELL_PROF_SCHUR0 = 3,    /* local-Schur block Sbar on the fine grid */
+  CELL_PROF_COUPLING = 4,  /* coupling block B */
+  CELL_PROF_COARSE = 5,    /* every operator apply on coarse multigrid levels */
+  CELL_PROF_KRYLOV = 6,    /* Gram-Schmidt dot / update passes */
+  CELL_PROF_CLASSES = 7
+} cell_prof_class;
+
 typedef struct cell_stats {
   int status;               /* cell_status of the solve */
   int iters[9];             /* GMRES iterations per load (all refinement steps) */
-  int refinements;          /* FP64 refinement steps taken (MIXED) */
+  int refinements;          /* FP64 restarts / refinement steps taken */
   int nlevels_u, nlevels_phi;
   double rel_residual[9];   /* final true relative residual per load (FP64) */
   double solve_ms;          /* host wall time of cell_solve */
-  double apply_ms;          /* profile: summed device time of full-operator applies */
-  int apply_count;          /* profile: number of full-operator applies timed */
-  double smooth_ms;         /* profile: summed device time of block-operator applies */
-  int smooth_count;
+  double class_ms[CELL_PROF_CLASSES];   /* profile: summed device time per class */
+  int class_count[CELL_PROF_CLASSES];   /* profile: launches timed per class */
+  long long class_units[CELL_PROF_CLASSES]; /* profile: sum over timed launches of the
+                                           number of loads each launch processed */
 } cell_stats;
 
 typedef struct cell_handle cell_handle;
@@ -187,6 +199,10 @@ int cell_get_rho(cell_handle* h, double* out);
  * 4*n + c, local node n = a + 2b + 4c at corner (a,b,c)) and the 8x8 local
  * Schur complement S0 for the material and grid of d (d->input unused). */
 int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]);
+
+/* Number of kernels this library has launched in the calling process so far
+ * (all handles, all threads); lets a caller count the launches of a region. */
+long long cell_launch_count(void);
 
 void cell_destroy(cell_handle* h);
 const char* cell_status_str(int status);

@@ -25,7 +25,8 @@ CELL_F32, CELL_F64 = 0, 1
 EXPORTS = [
     "cell_default_options", "cell_setup", "cell_solve", "cell_homogenise", "cell_sensitivity",
     "cell_dh", "cell_get_solution", "cell_apply", "cell_rhs", "cell_get_rho",
-    "cell_element_matrices", "cell_destroy", "cell_status_str", "cell_last_error",
+    "cell_element_matrices", "cell_launch_count", "cell_destroy", "cell_status_str",
+    "cell_last_error",
 ]
 
 
@@ -49,12 +50,16 @@ class cell_desc(C.Structure):
     ]
 
 
+PROF_CLASSES = ["full32", "full64", "elastic0", "schur0", "coupling", "coarse", "krylov"]
+
+
 class cell_stats(C.Structure):
     _fields_ = [
         ("status", C.c_int), ("iters", C.c_int * 9), ("refinements", C.c_int),
         ("nlevels_u", C.c_int), ("nlevels_phi", C.c_int), ("rel_residual", C.c_double * 9),
-        ("solve_ms", C.c_double), ("apply_ms", C.c_double), ("apply_count", C.c_int),
-        ("smooth_ms", C.c_double), ("smooth_count", C.c_int),
+        ("solve_ms", C.c_double), ("class_ms", C.c_double * len(PROF_CLASSES)),
+        ("class_count", C.c_int * len(PROF_CLASSES)),
+        ("class_units", C.c_longlong * len(PROF_CLASSES)),
     ]
 
 
@@ -94,6 +99,8 @@ def load(path: str = LIB_PATH):
     lib.cell_destroy.restype = None
     lib.cell_status_str.argtypes = [C.c_int]
     lib.cell_status_str.restype = C.c_char_p
+    lib.cell_launch_count.argtypes = []
+    lib.cell_launch_count.restype = C.c_longlong
     lib.cell_last_error.argtypes = []
     lib.cell_last_error.restype = C.c_char_p
     for name in ("cell_setup", "cell_solve", "cell_homogenise", "cell_sensitivity", "cell_dh",
@@ -224,6 +231,10 @@ def cell_element_matrices(desc: cell_desc):
         C.byref(desc), K0.ctypes.data_as(C.POINTER(C.c_double)),
         S0.ctypes.data_as(C.POINTER(C.c_double))))
     return K0.reshape(32, 32), S0.reshape(8, 8)
+
+
+def cell_launch_count() -> int:
+    return int(load().cell_launch_count())
 
 
 def cell_destroy(h):

@@ -51,10 +51,9 @@ class Cell:
             "refinements": st.refinements,
             "rel_residual": list(st.rel_residual),
             "solve_ms": st.solve_ms,
-            "apply_ms": st.apply_ms,
-            "apply_count": st.apply_count,
-            "smooth_ms": st.smooth_ms,
-            "smooth_count": st.smooth_count,
+            "class_ms": dict(zip(B.PROF_CLASSES, list(st.class_ms))),
+            "class_count": dict(zip(B.PROF_CLASSES, list(st.class_count))),
+            "class_units": dict(zip(B.PROF_CLASSES, list(st.class_units))),
             "nlevels_u": st.nlevels_u,
             "nlevels_phi": st.nlevels_phi,
         }

@@ -25,15 +25,17 @@ struct NodeIdx {
   i64 n, nn;
 };
 
+// Grid (ceil(nx*ny / kBlock), nz, nrhs): thread -> node (i, j, k) with 32-bit
+// index arithmetic; returns false past the end of the xy plane.
 __device__ __forceinline__ bool node_index(int nx, int ny, int nz, NodeIdx& t) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nx * ny) return false;
+  const int j = p / nx;
+  const int i = p - j * nx;
+  const int k = blockIdx.y;
   const i64 nxy = (i64)nx * ny;
   t.nn = nxy * nz;
-  t.n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t.n >= t.nn) return false;
-  const int i = (int)(t.n % nx);
-  const i64 q = t.n / nx;
-  const int j = (int)(q % ny);
-  const int k = (int)(q / ny);
+  t.n = (i64)k * nxy + p;
   t.xo[0] = i == 0 ? nx - 1 : i - 1;
   t.xo[1] = i;
   t.xo[2] = i == nx - 1 ? 0 : i + 1;
@@ -77,7 +79,7 @@ __device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const Nod
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
-  const int r = blockIdx.y;
+  const int r = blockIdx.z;
   if (a.active && !a.active[r]) return;
   NodeIdx t;
   if (!node_index(a.nx, a.ny, a.nz, t)) return;
@@ -124,7 +126,7 @@ k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM>
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_apply_fixed_ld(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
-  const int r = blockIdx.y;
+  const int r = blockIdx.z;
   if (a.active && !a.active[r]) return;
   NodeIdx t;
   if (!node_index(a.nx, a.ny, a.nz, t)) return;
@@ -162,58 +164,88 @@ k_apply_fixed_ld(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> 
   epilogue<T, NCO, MODE>(a, r, t, acc, dold);
 }
 
-// Per-element (Galerkin) matrices on a coarse level.
-template <typename T, int NC, int MODE>
-__global__ void __launch_bounds__(kBlock) k_apply_elem(const ApplyArgs<T> a) {
-  const int r = blockIdx.y;
-  if (a.active && !a.active[r]) return;
+// Per-element (Galerkin) matrices on a coarse level.  One thread per node
+// and group of RG loads (grid z = 9 / RG groups): each element row block
+// (NC x 8NC values, entry-major in memory so a warp's loads coalesce) is read
+// once per group and applied to the group's loads.  Large levels use RG = 3
+// (fewer matrix reads), small levels RG = 1 (more parallelism).
+template <typename T, int NC, int RG, int MODE>
+__global__ void __launch_bounds__(kBlock) k_apply_elem(const ApplyArgs<T> a, int nrhs) {
   NodeIdx t;
   if (!node_index(a.nx, a.ny, a.nz, t)) return;
-  const T* X = a.x + r * a.xs;
+  const int r0 = blockIdx.z * RG;
+  bool on[RG];
+  bool any = false;
+#pragma unroll
+  for (int g = 0; g < RG; ++g) {
+    on[g] = (r0 + g < nrhs) && !(a.active && !a.active[r0 + g]);
+    any = any || on[g];
+  }
+  if (!any) return;
   const i64 ne = t.nn;
-  T acc[NC];
+  constexpr int R = 8 * NC;
+  T acc[RG][NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) acc[c] = T(0);
+  for (int g = 0; g < RG; ++g)
 #pragma unroll
+    for (int c = 0; c < NC; ++c) acc[g][c] = T(0);
+#pragma unroll 1
   for (int e = 0; e < 8; ++e) {
     const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
     const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
-    const i64 el = t.xo[ex] + t.yo[ey] + t.zo[ez];
-    const T* K = a.ke + (i64)(la * NC) * (8 * NC) * ne + el;
+    // neighbour offsets of this element's corners, by select (no local arrays)
+    const i64 x0 = ex ? t.xo[1] : t.xo[0], x1 = ex ? t.xo[2] : t.xo[1];
+    const i64 y0 = ey ? t.yo[1] : t.yo[0], y1 = ey ? t.yo[2] : t.yo[1];
+    const i64 z0 = ez ? t.zo[1] : t.zo[0], z1 = ez ? t.zo[2] : t.zo[1];
+    const i64 el = x0 + y0 + z0;
+    const T* K = a.ke + (i64)(la * NC) * R * ne + el;
+    T km[NC][R];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
-      const i64 m = t.xo[ex + (b & 1)] + t.yo[ey + ((b >> 1) & 1)] + t.zo[ez + (b >> 2)];
+    for (int c = 0; c < NC; ++c)
 #pragma unroll
-      for (int d = 0; d < NC; ++d) {
-        const T xv = __ldg(X + d * t.nn + m);
+      for (int b = 0; b < R; ++b) km[c][b] = __ldg(K + (i64)(c * R + b) * ne);
+    int m[8];
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
-          acc[c] = fma(__ldg(K + (i64)(c * 8 * NC + b * NC + d) * ne), xv, acc[c]);
-      }
+    for (int b = 0; b < 8; ++b)
+      m[b] = (int)(((b & 1) ? x1 : x0) + (((b >> 1) & 1) ? y1 : y0) + ((b >> 2) ? z1 : z0));
+#pragma unroll
+    for (int g = 0; g < RG; ++g) {
+      if (!on[g]) continue;
+      const T* X = a.x + (r0 + g) * a.xs;
+#pragma unroll
+      for (int b = 0; b < 8; ++b)
+#pragma unroll
+        for (int d = 0; d < NC; ++d) {
+          const T xv = __ldg(X + d * t.nn + m[b]);
+#pragma unroll
+          for (int c = 0; c < NC; ++c) acc[g][c] = fma(km[c][b * NC + d], xv, acc[g][c]);
+        }
     }
   }
-  T dold[NC];
 #pragma unroll
-  for (int c = 0; c < NC; ++c)
-    dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? X[c * t.nn + t.n] : T(0);
-  epilogue<T, NC, MODE>(a, r, t, acc, dold);
+  for (int g = 0; g < RG; ++g) {
+    if (!on[g]) continue;
+    const int r = r0 + g;
+    T dold[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? a.x[r * a.xs + c * t.nn + t.n] : T(0);
+    epilogue<T, NC, MODE>(a, r, t, acc[g], dold);
+  }
 }
 
-inline dim3 grid_for(const ApplyArgs<float>& a, int nrhs) {
-  const i64 nn = (i64)a.nx * a.ny * a.nz;
-  return dim3((unsigned)((nn + kBlock - 1) / kBlock), (unsigned)nrhs);
-}
-inline dim3 grid_for(const ApplyArgs<double>& a, int nrhs) {
-  const i64 nn = (i64)a.nx * a.ny * a.nz;
-  return dim3((unsigned)((nn + kBlock - 1) / kBlock), (unsigned)nrhs);
+template <typename T>
+inline dim3 grid_for(const ApplyArgs<T>& a, int nrhs) {
+  const int plane = a.nx * a.ny;
+  return dim3((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)a.nz, (unsigned)nrhs);
 }
 
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEG, int MODE>
 void launch_fixed(const ApplyArgs<T>& a, const FixedMat<T, NCM>& M, int nrhs, cudaStream_t s) {
   if constexpr (sizeof(T) == 4)
-    k_apply_fixed_pre<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
+    note_launch(), k_apply_fixed_pre<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
   else
-    k_apply_fixed_ld<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
+    note_launch(), k_apply_fixed_ld<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
 }
 
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEG>
@@ -251,15 +283,22 @@ void apply_ss(const ApplyArgs<T>& a, const FixedMat<T, 1>& M, int mode, int nrhs
   dispatch_fixed<T, 1, 1, 1, 0, 0, false>(a, M, mode, nrhs, s);
 }
 
+template <typename T, int NC, int RG>
+void launch_elem(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
+  const dim3 g = grid_for(a, (nrhs + RG - 1) / RG);
+  switch (mode) {
+    case AM_LINEAR: note_launch(), k_apply_elem<T, NC, RG, AM_LINEAR><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    case AM_CHEB: note_launch(), k_apply_elem<T, NC, RG, AM_CHEB><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    case AM_CHEB_LAST: note_launch(), k_apply_elem<T, NC, RG, AM_CHEB_LAST><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    default: note_launch(), k_apply_elem<T, NC, RG, AM_RESID_CHEB0><<<g, kBlock, 0, s>>>(a, nrhs); break;
+  }
+}
+
 template <typename T, int NC>
 void apply_elem(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
-  const dim3 g = grid_for(a, nrhs);
-  switch (mode) {
-    case AM_LINEAR: k_apply_elem<T, NC, AM_LINEAR><<<g, kBlock, 0, s>>>(a); break;
-    case AM_CHEB: k_apply_elem<T, NC, AM_CHEB><<<g, kBlock, 0, s>>>(a); break;
-    case AM_CHEB_LAST: k_apply_elem<T, NC, AM_CHEB_LAST><<<g, kBlock, 0, s>>>(a); break;
-    default: k_apply_elem<T, NC, AM_RESID_CHEB0><<<g, kBlock, 0, s>>>(a); break;
-  }
+  const long long nn = (long long)a.nx * a.ny * a.nz;
+  if (nn >= 16384) launch_elem<T, NC, 3>(a, mode, nrhs, s);
+  else launch_elem<T, NC, 1>(a, mode, nrhs, s);
 }
 
 #define INST(T)                                                                                   \

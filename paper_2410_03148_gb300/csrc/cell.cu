@@ -21,6 +21,8 @@
 using cell::i64;
 using cell::kNvMax;
 
+std::atomic<long long> cell::g_launches{0};
+
 namespace {
 
 thread_local std::string g_last_error;
@@ -73,7 +75,9 @@ struct Arena {
 struct Prof {
   bool on = false;
   std::vector<cudaEvent_t> pool;
-  std::vector<std::pair<int, int>> marks[2];  // (start event, stop event) per class
+  std::vector<std::pair<int, int>> marks[CELL_PROF_CLASSES];  // (start, stop) per class
+  long long units[CELL_PROF_CLASSES] = {0};
+  int cur_units = 9;   // loads processed by the launches being timed
   size_t used = 0;
   cudaEvent_t get() {
     if (used == pool.size()) {
@@ -94,9 +98,10 @@ struct Prof {
     const int i1 = (int)used;
     cudaEventRecord(get(), s);
     marks[cls].push_back({i0, i1});
+    units[cls] += cur_units;
   }
-  void collect(double* ms, int* cnt) {
-    for (int c = 0; c < 2; ++c) {
+  void collect(double* ms, int* cnt, long long* un) {
+    for (int c = 0; c < CELL_PROF_CLASSES; ++c) {
       double t = 0.0;
       for (auto& m : marks[c]) {
         float f = 0.f;
@@ -105,6 +110,8 @@ struct Prof {
       }
       ms[c] = t;
       cnt[c] = (int)marks[c].size();
+      un[c] = units[c];
+      units[c] = 0;
       marks[c].clear();
     }
     used = 0;
@@ -114,7 +121,6 @@ struct Prof {
   }
 };
 
-enum { PROF_FULL = 0, PROF_BLOCK = 1 };
 
 template <typename T>
 struct Level {
@@ -173,6 +179,9 @@ struct cell_handle {
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr;
   double *partial = nullptr, *red = nullptr, *red2 = nullptr;
   int nblk = 0;
+  // per-load magnitude of the element contributions, sqrt(sum rho_e^2) |K0 Zbar^I|:
+  // right-hand sides or residuals below 1e-13 of it are rounding noise
+  double bfloor[9];
   // Krylov-scalar state (FP64, device)
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *hcol = nullptr, *hnorm = nullptr;
   double *resid = nullptr, *invscale = nullptr, *tolabs = nullptr, *ybuf = nullptr, *beta2 = nullptr;
@@ -219,7 +228,7 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
     a.ke = L.ke;
     cell::apply_elem<T, NC>(a, mode, 9, h->st);
   }
-  h->prof.end(PROF_BLOCK, ip, h->st);
+  h->prof.end(l > 0 ? CELL_PROF_COARSE : (NC == 3 ? CELL_PROF_ELASTIC0 : CELL_PROF_SCHUR0), ip, h->st);
 }
 
 // Dense assembly of a level's operator on the host (coarsest level only).
@@ -445,7 +454,9 @@ void precond(cell_handle* h, const T* v, T* z, const int* mask) {
   a.x = z; a.xs = len; a.y = K.tphi; a.ys = nn; a.b = v + 3 * nn; a.bs = len;
   a.alpha = T(1); a.beta = T(1); a.rho = K.rho; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
   a.active = mask;
+  const int ip = h->prof.begin(h->st);
   cell::apply_pu<T>(a, K.K0, 9, h->st);
+  h->prof.end(CELL_PROF_COUPLING, ip, h->st);
   block_solve<T, 1>(h, K.mgp, h->d.opt.vcycles_phi, K.tphi, nn, z + 3 * nn, len, K.rp, K.ep, mask);
 }
 
@@ -458,7 +469,7 @@ void apply_full_T(cell_handle* h, const T* x, i64 xs, T* y, i64 ys, const T* b, 
   const int ip = h->prof.begin(h->st);
   if constexpr (sizeof(T) == 4) cell::apply_full<T>(a, h->kf.K0, cell::AM_LINEAR, nrhs, h->st);
   else cell::apply_full<T>(a, h->kd.K0, cell::AM_LINEAR, nrhs, h->st);
-  h->prof.end(PROF_FULL, ip, h->st);
+  h->prof.end(sizeof(T) == 4 ? CELL_PROF_FULL32 : CELL_PROF_FULL64, ip, h->st);
 }
 
 template <typename T>
@@ -518,9 +529,10 @@ int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
   int ran[9];
   CK(cudaMemcpyAsync(ran, h->ranmask, sizeof(ran), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  bool any = false;
-  for (int q = 0; q < 9; ++q) any = any || ran[q];
-  if (!any) return CELL_OK;
+  int nran = 0;
+  for (int q = 0; q < 9; ++q) nran += ran[q] ? 1 : 0;
+  if (!nran) return CELL_OK;
+  h->prof.cur_units = nran;
   int j = 0;
   for (; j < m; ++j) {
     T* vj = K.V + (i64)j * vstride;
@@ -528,6 +540,7 @@ int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
     precond<T>(h, vj, K.z, h->active);
     apply_full_T<T>(h, K.z, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
     // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2 (with |w|^2)
+    const int ipk = h->prof.begin(s);
     cell::multidot<T>(K.V, vstride, len, j + 1, w, len, len, h->partial, nblk, kNvMax, 9, h->active, s);
     cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->hcol, 0, 9, h->active, s);
     cell::update<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, 1, h->partial, nblk, 9, h->active, s);
@@ -536,16 +549,19 @@ int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
     cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->active, s);
     // hcol += second-pass coefficients (a one-block "reduction" of ybuf)
     cell::reduce_partials(h->ybuf, 1, j + 1, kNvMax, h->hcol, 1, 9, h->active, s);
+    h->prof.end(CELL_PROF_KRYLOV, ipk, s);
     cell::givens_step(h->H, h->cs, h->sn, h->g, h->hcol, h->hnorm, j, m, h->active, h->resid,
                       h->tolabs, h->invscale, h->kcount, 9, s);
     cell::scale_vec<T>(w, len, len, h->invscale, 9, s);
     int act[9];
     CK(cudaMemcpyAsync(act, h->active, sizeof(act), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    bool more = false;
-    for (int q = 0; q < 9; ++q) more = more || act[q];
-    if (!more) break;
+    int nact = 0;
+    for (int q = 0; q < 9; ++q) nact += act[q] ? 1 : 0;
+    if (!nact) break;
+    h->prof.cur_units = nact;
   }
+  h->prof.cur_units = nran;
   cell::backsolve(h->H, h->g, h->kcount, m, h->ybuf, 9, h->ranmask, s);
   cell::lincomb<T>(K.V, vstride, len, h->ybuf, h->kcount, kNvMax, K.u, len, len, 9, h->ranmask, s);
   precond<T>(h, K.u, K.z, h->ranmask);
@@ -663,6 +679,17 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(A.alloc(&h->want, 9));
   CKS(A.alloc(&h->ranmask, 9));
   CK(cudaMemsetAsync(h->x64, 0, 9 * len * sizeof(double), h->st));
+  {
+    double srho2 = 0.0;
+    cell::sum_reduce(h->rho64, nn, h->partial, h->nblk, h->red, h->st, 1);
+    CK(cudaMemcpyAsync(&srho2, h->red, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CK(cudaStreamSynchronize(h->st));
+    for (int I = 0; I < 9; ++I) {
+      double f2 = 0.0;
+      for (int a = 0; a < 32; ++a) f2 += h->F[a * 9 + I] * h->F[a * 9 + I];
+      h->bfloor[I] = 1e-13 * std::sqrt(srho2 * f2);
+    }
+  }
   // the FP64 operator serves the refinement residual in every precision mode
   std::memcpy(h->kd.K0.k, h->K0, sizeof(h->kd.K0.k));
   std::memcpy(h->kd.S0.k, h->S0, sizeof(h->kd.S0.k));
@@ -708,8 +735,8 @@ int solve_impl(cell_handle* h, cell_stats* st) {
     for (int q = 0; q < 9; ++q) {
       rn2[q] = tmp[q * kNvMax];
       const double bn = std::sqrt(bn2[q]), rn = std::sqrt(rn2[q]);
-      S.rel_residual[q] = bn > 0 ? rn / bn : 0.0;
-      want[q] = ((o.load_mask >> q) & 1) && bn > 0 && rn > o.tol * bn;
+      S.rel_residual[q] = bn > h->bfloor[q] ? rn / bn : 0.0;
+      want[q] = ((o.load_mask >> q) & 1) && rn > std::max(o.tol * bn, h->bfloor[q]);
       any = any || want[q];
       maxit = std::max(maxit, S.iters[q]);
       const double inner = sizeof(T) == 4 ? o.inner_tol : o.tol * 0.5;
@@ -724,6 +751,7 @@ int solve_impl(cell_handle* h, cell_stats* st) {
     CKS(gmres_cycle<T>(h, tolabs, S.iters));
     ++refine;
     // FP64 residual of the updated iterate: r = bhat - Ahat x
+    h->prof.cur_units = 9;
     apply_full_T<double>(h, h->x64, len, h->r64, len, h->b64, len, -1.0, 1.0, nullptr, 9);
   }
   // null-space projection (mean displacement and potential per load)
@@ -737,15 +765,7 @@ int solve_impl(cell_handle* h, cell_stats* st) {
   S.status = status;
   S.nlevels_u = (int)kry<T>(h).mgu.lv.size();
   S.nlevels_phi = (int)kry<T>(h).mgp.lv.size();
-  if (h->prof.on) {
-    double ms[2];
-    int cnt[2];
-    h->prof.collect(ms, cnt);
-    S.apply_ms = ms[0];
-    S.apply_count = cnt[0];
-    S.smooth_ms = ms[1];
-    S.smooth_count = cnt[1];
-  }
+  if (h->prof.on) h->prof.collect(S.class_ms, S.class_count, S.class_units);
   h->solved = (status == CELL_OK);
   h->last = S;
   if (st) *st = S;
@@ -772,7 +792,7 @@ void cell_default_options(cell_options* o) {
   o->vcycles_u = 1;
   o->vcycles_phi = 1;
   o->cheb_degree = 3;
-  o->cheb_lo = 0.1;
+  o->cheb_lo = 0.05;
   o->cheb_hi = 1.0;
   o->schur_shift = 1e-10;
   o->coarse_dofs = 200;
@@ -995,5 +1015,7 @@ const char* cell_status_str(int s) {
 }
 
 const char* cell_last_error(void) { return g_last_error.c_str(); }
+
+long long cell_launch_count(void) { return cell::g_launches.load(); }
 
 }  // extern "C"

@@ -151,13 +151,14 @@ k_gram9(const double* __restrict__ u, const double* __restrict__ v, i64 nn,
   }
 }
 
+template <bool SQ>
 __global__ void __launch_bounds__(kB)
 k_sum(const double* __restrict__ x, i64 n, double* __restrict__ partial) {
   __shared__ double sh[kWarps];
   const i64 chunk = (n + gridDim.x - 1) / gridDim.x;
   const i64 lo = (i64)blockIdx.x * chunk, hi = lo + chunk < n ? lo + chunk : n;
   double s = 0.0;
-  for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += x[k];
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += SQ ? x[k] * x[k] : x[k];
   s = block_sum(s, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
@@ -212,40 +213,42 @@ template <typename Tin>
 void ersatz(const Tin* phi, int nx, int ny, int nz, double rho_void, double eta, float* rho32,
             double* rho64, cudaStream_t s) {
   const i64 nn = (i64)nx * ny * nz;
-  k_ersatz<Tin><<<nb(nn), kB, 0, s>>>(phi, nx, ny, nz, rho_void, eta, rho32, rho64);
+  note_launch(), k_ersatz<Tin><<<nb(nn), kB, 0, s>>>(phi, nx, ny, nz, rho_void, eta, rho32, rho64);
 }
 
 template <typename Tin>
 void rho_copy(const Tin* in, i64 n, float* rho32, double* rho64, int* bad, cudaStream_t s) {
-  k_rho_copy<Tin><<<nb(n), kB, 0, s>>>(in, n, rho32, rho64, bad);
+  note_launch(), k_rho_copy<Tin><<<nb(n), kB, 0, s>>>(in, n, rho32, rho64, bad);
 }
 
 void rhs9(const double* rho, const RhsParams& F, int mask, double* b, int nx, int ny, int nz,
           cudaStream_t s) {
   const i64 nn = (i64)nx * ny * nz;
-  k_rhs9<<<nb(nn), kB, 0, s>>>(rho, F, mask, b, nx, ny, nz);
+  note_launch(), k_rhs9<<<nb(nn), kB, 0, s>>>(rho, F, mask, b, nx, ny, nz);
 }
 
 void comp_sums(const double* x, i64 nn, int nrhs, double* partial, int nblk, double* out,
                cudaStream_t s) {
-  k_comp_sums<<<dim3(nblk, nrhs * 4), kB, 0, s>>>(x, nn, partial);
+  note_launch(), k_comp_sums<<<dim3(nblk, nrhs * 4), kB, 0, s>>>(x, nn, partial);
   reduce_partials(partial, nblk, 1, 1, out, 0, nrhs * 4, nullptr, s);
 }
 
 void sub_means(double* x, i64 nn, int nrhs, const double* sums, cudaStream_t s) {
   unsigned g = nb(nn);
   if (g > 2048) g = 2048;
-  k_sub_means<<<dim3(g, nrhs * 4), kB, 0, s>>>(x, nn, sums);
+  note_launch(), k_sub_means<<<dim3(g, nrhs * 4), kB, 0, s>>>(x, nn, sums);
 }
 
 void gram9(const double* u, const double* v, i64 nn, double* partial, int nblk, double* out,
            cudaStream_t s) {
-  k_gram9<<<dim3(nblk, 9), kB, 0, s>>>(u, v, nn, partial);
+  note_launch(), k_gram9<<<dim3(nblk, 9), kB, 0, s>>>(u, v, nn, partial);
   reduce_partials(partial, nblk, 9, 9, out, 0, 9, nullptr, s);
 }
 
-void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s) {
-  k_sum<<<nblk, kB, 0, s>>>(x, n, partial);
+void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s,
+                int squares) {
+  if (squares) note_launch(), k_sum<true><<<nblk, kB, 0, s>>>(x, n, partial);
+  else note_launch(), k_sum<false><<<nblk, kB, 0, s>>>(x, n, partial);
   reduce_partials(partial, nblk, 1, 1, out, 0, 1, nullptr, s);
 }
 
@@ -253,7 +256,7 @@ template <typename T>
 void sensitivity(const double* y, const double* rho, const double* K0dev, const SensParams& P, T* g,
                  int nx, int ny, int nz, int times_rho, cudaStream_t s) {
   const i64 nn = (i64)nx * ny * nz;
-  k_sens<T><<<(unsigned)((nn + kWarps - 1) / kWarps), kB, 0, s>>>(y, rho, K0dev, P, g, nx, ny, nz,
+  note_launch(), k_sens<T><<<(unsigned)((nn + kWarps - 1) / kWarps), kB, 0, s>>>(y, rho, K0dev, P, g, nx, ny, nz,
                                                                   times_rho);
 }
 

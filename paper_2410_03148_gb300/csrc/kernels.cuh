@@ -2,11 +2,17 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 
 namespace cell {
 
 typedef long long i64;
+
+// Count of kernels launched by the library (cell_launch_count()).
+extern std::atomic<long long> g_launches;
+inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 // Leading dimension of the per-load Krylov scalars (Gram-Schmidt columns,
 // partial sums); bounds the GMRES restart length.
@@ -143,8 +149,9 @@ void sub_means(double* x, i64 nn, int nrhs, const double* sums, cudaStream_t s);
 // G_IJ (+)= sum_n sum_c sgn_c u^I_c v^J_c, sgn = -1 for the potential component
 void gram9(const double* u, const double* v, i64 nn, double* partial, int nblk, double* out,
            cudaStream_t s);
-// out[0] = sum of x[0..n)  (device scalar)
-void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s);
+// out[0] = sum of x[0..n) (or of the squares)  (device scalar)
+void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s,
+                int squares = 0);
 // g_e = (rho_e if times_rho) * sum_IJ G_IJ W_e^I . K0 W_e^J, W = Zbar + y_e
 template <typename T> void sensitivity(const double* y, const double* rho, const double* K0dev,
                                        const SensParams& P, T* g, int nx, int ny, int nz,

@@ -32,25 +32,62 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
   return t;
 }
 
-// grid (nblk, nrhs); each block covers a contiguous chunk of len.
+// Per-thread partial sums use the vector type T (FP32 for the mixed path:
+// FP64 arithmetic runs at 1/64 of the FP32 rate on this part and would cap
+// the reductions far below HBM bandwidth); block and grid sums are FP64.
+
+// Reduce G per-thread values over the block; thread i < G gets total i.
+template <int G>
+__device__ __forceinline__ void block_sum_many(double (&v)[G], double (*sh)[G]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < G; ++i) v[i] = warp_sum(v[i]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < G; ++i) sh[wid][i] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < G) {
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += sh[w][threadIdx.x];
+    v[0] = t;
+  }
+}
+
+constexpr int kGrp = 8;
+
+// grid (nblk, nrhs, ceil(nv / kGrp)); each block computes the partial dots of
+// w with the kGrp basis vectors of its group over a contiguous chunk of len.
 template <typename T>
 __global__ void __launch_bounds__(kB)
 k_multidot(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const T* __restrict__ w,
            i64 wstride, i64 len, double* __restrict__ partial, int nvmax, const int* active) {
-  __shared__ double sh[kWarps];
+  __shared__ double sh[kWarps][kGrp];
   const int q = blockIdx.y;
   if (active && !active[q]) return;
+  const int g0 = blockIdx.z * kGrp;
+  const int ng = nv - g0 < kGrp ? nv - g0 : kGrp;
   const i64 chunk = (len + gridDim.x - 1) / gridDim.x;
   const i64 lo = (i64)blockIdx.x * chunk;
   const i64 hi = lo + chunk < len ? lo + chunk : len;
   const T* W = w + q * wstride;
-  for (int i = 0; i < nv; ++i) {
-    const T* Vi = V + i * vstride + q * rstride;
-    double s = 0.0;
-    for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += (double)Vi[k] * (double)W[k];
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + i] = s;
+  const T* V0 = V + q * rstride + (i64)g0 * vstride;
+  T acc[kGrp];
+#pragma unroll
+  for (int i = 0; i < kGrp; ++i) acc[i] = T(0);
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
+    const T wk = W[k];
+#pragma unroll
+    for (int i = 0; i < kGrp; ++i)
+      if (i < ng) acc[i] = fma(V0[(i64)i * vstride + k], wk, acc[i]);
   }
+  double d[kGrp];
+#pragma unroll
+  for (int i = 0; i < kGrp; ++i) d[i] = (double)acc[i];
+  block_sum_many<kGrp>(d, sh);
+  if (threadIdx.x < ng) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + g0 + threadIdx.x] = d[0];
 }
 
 // One warp per (rhs, i): fixed-order sum over blocks.
@@ -67,43 +104,44 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nblk, 
   if (lane == 0) out[q * nvmax + i] = accumulate ? out[q * nvmax + i] + s : s;
 }
 
-// w -= sum_i h_i V_i over this block's chunk, then partial dots or norm.
+// w -= sum_i h_i V_i; mode 2 also writes block-partial |w_new|^2.
 template <typename T>
 __global__ void __launch_bounds__(kB)
 k_update(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const double* __restrict__ h,
          int nvmax, T* __restrict__ w, i64 wstride, i64 len, int mode, double* __restrict__ partial,
          const int* active) {
-  __shared__ double sh[kWarps];
-  __shared__ double hs[64];
+  __shared__ double sh[kWarps][1];
+  __shared__ T hs[64];
   const int q = blockIdx.y;
   if (active && !active[q]) return;
-  for (int i = threadIdx.x; i < nv; i += kB) hs[i] = h[q * nvmax + i];
+  for (int i = threadIdx.x; i < 64; i += kB) hs[i] = i < nv ? (T)h[q * nvmax + i] : T(0);
   __syncthreads();
   const i64 chunk = (len + gridDim.x - 1) / gridDim.x;
   const i64 lo = (i64)blockIdx.x * chunk;
   const i64 hi = lo + chunk < len ? lo + chunk : len;
   T* W = w + q * wstride;
   const T* V0 = V + q * rstride;
-  double nrm = 0.0;
+  T nrm = T(0);
   for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
-    double acc = (double)W[k];
-    for (int i = 0; i < nv; ++i) acc -= hs[i] * (double)V0[i * vstride + k];
-    const T v = (T)acc;
-    W[k] = v;
-    nrm += (double)v * (double)v;
+    T x = W[k];
+    const T* vp = V0 + k;
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+      const T a0 = vp[(i64)i * vstride], a1 = vp[(i64)(i + 1) * vstride];
+      const T a2 = vp[(i64)(i + 2) * vstride], a3 = vp[(i64)(i + 3) * vstride];
+      x = fma(-hs[i], a0, x);
+      x = fma(-hs[i + 1], a1, x);
+      x = fma(-hs[i + 2], a2, x);
+      x = fma(-hs[i + 3], a3, x);
+    }
+    for (; i < nv; ++i) x = fma(-hs[i], vp[(i64)i * vstride], x);
+    W[k] = x;
+    nrm = fma(x, x, nrm);
   }
   if (mode == 2) {
-    nrm = block_sum(nrm, sh);
-    if (threadIdx.x == 0) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + 0] = nrm;
-  } else if (mode == 1) {
-    // second pass over the chunk (now cache-resident) for the reorthogonalisation dots
-    for (int i = 0; i < nv; ++i) {
-      const T* Vi = V0 + i * vstride;
-      double s = 0.0;
-      for (i64 k = lo + threadIdx.x; k < hi; k += kB) s += (double)Vi[k] * (double)W[k];
-      s = block_sum(s, sh);
-      if (threadIdx.x == 0) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + i] = s;
-    }
+    double d[1] = {(double)nrm};
+    block_sum_many<1>(d, sh);
+    if (threadIdx.x == 0) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + 0] = d[0];
   }
 }
 
@@ -252,14 +290,15 @@ inline unsigned stream_blocks(i64 len) {
 template <typename T>
 void multidot(const T* V, i64 vstride, i64 rstride, int nv, const T* w, i64 wstride, i64 len,
               double* partial, int nblk, int nvmax, int nrhs, const int* active, cudaStream_t s) {
-  k_multidot<T><<<dim3(nblk, nrhs), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride, len, partial,
-                                                 nvmax, active);
+  const unsigned ng = (unsigned)((nv + kGrp - 1) / kGrp);
+  note_launch(), k_multidot<T><<<dim3(nblk, nrhs, ng), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride,
+                                                                   len, partial, nvmax, active);
 }
 
 void reduce_partials(const double* partial, int nblk, int nv, int nvmax, double* out, int accumulate,
                      int nrhs, const int* active, cudaStream_t s) {
   const int wpb = 4;
-  k_reduce_partials<<<dim3((nv + wpb - 1) / wpb, nrhs), 32 * wpb, 0, s>>>(partial, nblk, nv, nvmax,
+  note_launch(), k_reduce_partials<<<dim3((nv + wpb - 1) / wpb, nrhs), 32 * wpb, 0, s>>>(partial, nblk, nv, nvmax,
                                                                          out, accumulate, active);
 }
 
@@ -267,53 +306,55 @@ template <typename T>
 void update(const T* V, i64 vstride, i64 rstride, int nv, const double* h, int nvmax, T* w,
             i64 wstride, i64 len, int mode, double* partial, int nblk, int nrhs, const int* active,
             cudaStream_t s) {
-  k_update<T><<<dim3(nblk, nrhs), kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len,
-                                               mode, partial, active);
+  note_launch(), k_update<T><<<dim3(nblk, nrhs), kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w,
+                                                             wstride, len, mode == 2 ? 2 : 0,
+                                                             partial, active);
+  if (mode == 1) multidot<T>(V, vstride, rstride, nv, w, wstride, len, partial, nblk, nvmax, nrhs, active, s);
 }
 
 template <typename T>
 void scale_vec(T* w, i64 wstride, i64 len, const double* sc, int nrhs, cudaStream_t s) {
-  k_scale<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(w, wstride, len, sc);
+  note_launch(), k_scale<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(w, wstride, len, sc);
 }
 
 template <typename T>
 void lincomb(const T* V, i64 vstride, i64 rstride, const double* y, const int* kcount, int nvmax,
              T* u, i64 ustride, i64 len, int nrhs, const int* active, cudaStream_t s) {
-  k_lincomb<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(V, vstride, rstride, y, kcount, nvmax,
+  note_launch(), k_lincomb<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(V, vstride, rstride, y, kcount, nvmax,
                                                               u, ustride, len, active);
 }
 
 void givens_step(double* H, double* cs, double* sn, double* g, const double* hcol,
                  const double* hnorm2, int j, int m, int* active, double* resid,
                  const double* tolabs, double* invscale, int* kcount, int nrhs, cudaStream_t s) {
-  k_givens<<<1, 32, 0, s>>>(H, cs, sn, g, hcol, hnorm2, j, m, 64, active, resid, tolabs, invscale,
+  note_launch(), k_givens<<<1, 32, 0, s>>>(H, cs, sn, g, hcol, hnorm2, j, m, 64, active, resid, tolabs, invscale,
                             kcount, nrhs);
 }
 
 void backsolve(const double* H, const double* g, const int* kcount, int m, double* y, int nrhs,
                const int* mask, cudaStream_t s) {
-  k_backsolve<<<1, 32, 0, s>>>(H, g, kcount, m, y, 64, nrhs, mask);
+  note_launch(), k_backsolve<<<1, 32, 0, s>>>(H, g, kcount, m, y, 64, nrhs, mask);
 }
 
 void start_cycle(const double* beta2, double* g, int m, int* active, const int* want, double* resid,
                  double* invscale, const double* tolabs, int* kcount, int nrhs, cudaStream_t s) {
-  k_start_cycle<<<1, 32, 0, s>>>(beta2, g, m, 64, active, want, resid, invscale, tolabs, kcount, nrhs);
+  note_launch(), k_start_cycle<<<1, 32, 0, s>>>(beta2, g, m, 64, active, want, resid, invscale, tolabs, kcount, nrhs);
 }
 
 void to_f32_scaled(const double* r, i64 rs, float* v, i64 vs, i64 len, const double* sc, int nrhs,
                    const int* active, cudaStream_t s) {
-  k_to_f32<<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(r, rs, v, vs, len, sc, active);
+  note_launch(), k_to_f32<<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(r, rs, v, vs, len, sc, active);
 }
 
 template <typename T>
 void axpy_f64(double* x, i64 xs, const T* d, i64 ds, i64 len, const double* sc, int nrhs,
               const int* active, cudaStream_t s) {
-  k_axpy_f64<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(x, xs, d, ds, len, sc, active);
+  note_launch(), k_axpy_f64<T><<<dim3(stream_blocks(len), nrhs), kB, 0, s>>>(x, xs, d, ds, len, sc, active);
 }
 
 template <typename T>
 void fill(T* p, i64 n, T v, cudaStream_t s) {
-  k_fill<T><<<stream_blocks(n), kB, 0, s>>>(p, n, v);
+  note_launch(), k_fill<T><<<stream_blocks(n), kB, 0, s>>>(p, n, v);
 }
 
 #define INST(T)                                                                                    \

@@ -197,37 +197,41 @@ __global__ void k_diag_inv(const T* __restrict__ fixedm, const T* __restrict__ r
 
 // lambda_max(diag(K_e)^-1 K_e) per element by power iteration on the
 // symmetric scaled matrix D^-1/2 K D^-1/2, max-reduced as float bits.
+// (FP32 arithmetic: this is a bound for a smoother, not a result.)
 template <typename T, int NC>
 __global__ void k_elem_lmax(const T* __restrict__ ke, i64 ne, unsigned int* out) {
   constexpr int R = 8 * NC;
   const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
-  double s[R], v[R], w[R];
+  float s[R], v[R], w[R];
+#pragma unroll
   for (int i = 0; i < R; ++i) {
-    const double dii = (double)ke[(i64)(i * R + i) * ne + e];
-    s[i] = dii > 0 ? rsqrt(dii) : 0.0;
-    v[i] = 1.0 + 0.1 * i;
+    const float dii = (float)ke[(i64)(i * R + i) * ne + e];
+    s[i] = dii > 0.f ? rsqrtf(dii) : 0.f;
+    v[i] = 1.f + 0.1f * i;
   }
-  double lam = 0.0;
-  for (int it = 0; it < 40; ++it) {
-    double nv = 0.0;
+  float lam = 0.f;
+  for (int it = 0; it < 30; ++it) {
+    float nv = 0.f, vv = 0.f, vw = 0.f;
+#pragma unroll
     for (int i = 0; i < R; ++i) {
-      double acc = 0.0;
-      for (int j = 0; j < R; ++j) acc += (double)ke[(i64)(i * R + j) * ne + e] * s[j] * v[j];
+      float acc = 0.f;
+#pragma unroll
+      for (int j = 0; j < R; ++j) acc = fmaf((float)__ldg(ke + (i64)(i * R + j) * ne + e), s[j] * v[j], acc);
       w[i] = s[i] * acc;
-      nv += w[i] * w[i];
     }
-    double vv = 0.0, vw = 0.0;
+#pragma unroll
     for (int i = 0; i < R; ++i) {
-      vv += v[i] * v[i];
-      vw += v[i] * w[i];
+      nv = fmaf(w[i], w[i], nv);
+      vv = fmaf(v[i], v[i], vv);
+      vw = fmaf(v[i], w[i], vw);
     }
-    lam = vv > 0 ? vw / vv : 0.0;
-    const double inv = nv > 0 ? rsqrt(nv) : 0.0;
+    lam = vv > 0.f ? vw / vv : 0.f;
+    const float inv = nv > 0.f ? rsqrtf(nv) : 0.f;
+#pragma unroll
     for (int i = 0; i < R; ++i) v[i] = w[i] * inv;
   }
-  const float lf = (float)lam;
-  if (lf > 0.f) atomicMax(out, __float_as_uint(lf));
+  if (lam > 0.f) atomicMax(out, __float_as_uint(lam));
 }
 
 // x = Ainv b per rhs and component block (nc comps of nn nodes, n = nc*nn).
@@ -249,46 +253,46 @@ __global__ void k_dense_solve(const T* __restrict__ Ainv, int n, const T* __rest
 template <typename T, int NC>
 void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds, const T* dinv, T c2, i64 nn,
                int nrhs, const int* active, cudaStream_t s) {
-  k_cheb_init<T, NC><<<dim3(nblocks(nn), nrhs), kB, 0, s>>>(b, bs, r, rs, d, ds, dinv, c2, nn, active);
+  note_launch(), k_cheb_init<T, NC><<<dim3(nblocks(nn), nrhs), kB, 0, s>>>(b, bs, r, rs, d, ds, dinv, c2, nn, active);
 }
 template <typename T, int NC>
 void axpy_view(T* x, i64 xs, const T* d, i64 ds, i64 nn, int nrhs, const int* active, cudaStream_t s) {
-  k_axpy_view<T, NC><<<dim3(nblocks(nn), nrhs), kB, 0, s>>>(x, xs, d, ds, nn, active);
+  note_launch(), k_axpy_view<T, NC><<<dim3(nblocks(nn), nrhs), kB, 0, s>>>(x, xs, d, ds, nn, active);
 }
 template <typename T, int NC>
 void restrict_fw(const T* rf, i64 rs, T* bc, i64 bs, int nx, int ny, int nz, int nrhs,
                  const int* active, cudaStream_t s) {
   const i64 ncn = (i64)(nx / 2) * (ny / 2) * (nz / 2);
-  k_restrict<T, NC><<<dim3(nblocks(ncn), nrhs), kB, 0, s>>>(rf, rs, bc, bs, nx, ny, nz, active);
+  note_launch(), k_restrict<T, NC><<<dim3(nblocks(ncn), nrhs), kB, 0, s>>>(rf, rs, bc, bs, nx, ny, nz, active);
 }
 template <typename T, int NC>
 void prolong_add(const T* xc, i64 cs, T* xf, i64 fs, int nx, int ny, int nz, int nrhs,
                  const int* active, cudaStream_t s) {
   const i64 nfn = (i64)nx * ny * nz;
-  k_prolong_add<T, NC><<<dim3(nblocks(nfn), nrhs), kB, 0, s>>>(xc, cs, xf, fs, nx, ny, nz, active);
+  note_launch(), k_prolong_add<T, NC><<<dim3(nblocks(nfn), nrhs), kB, 0, s>>>(xc, cs, xf, fs, nx, ny, nz, active);
 }
 template <typename T, int NC>
 void galerkin(const T* fixedm, const T* rho, const T* kef, T* kec, int ncx, int ncy, int ncz,
               cudaStream_t s) {
   const i64 nce = (i64)ncx * ncy * ncz;
-  k_galerkin<T, NC><<<dim3(nblocks(nce, 128), 8 * NC), 128, 0, s>>>(fixedm, rho, kef, kec, ncx, ncy, ncz);
+  note_launch(), k_galerkin<T, NC><<<dim3(nblocks(nce, 128), 8 * NC), 128, 0, s>>>(fixedm, rho, kef, kec, ncx, ncy, ncz);
 }
 template <typename T, int NC>
 void diag_inv(const T* fixedm, const T* rho, const T* ke, T* dinv, int nx, int ny, int nz,
               cudaStream_t s) {
   const i64 nn = (i64)nx * ny * nz;
-  k_diag_inv<T, NC><<<nblocks(nn), kB, 0, s>>>(fixedm, rho, ke, dinv, nx, ny, nz);
+  note_launch(), k_diag_inv<T, NC><<<nblocks(nn), kB, 0, s>>>(fixedm, rho, ke, dinv, nx, ny, nz);
 }
 template <typename T, int NC>
 void elem_lmax(const T* ke, i64 ne, unsigned int* out, cudaStream_t s) {
-  k_elem_lmax<T, NC><<<nblocks(ne, 64), 64, 0, s>>>(ke, ne, out);
+  note_launch(), k_elem_lmax<T, NC><<<nblocks(ne, 64), 64, 0, s>>>(ke, ne, out);
 }
 template <typename T>
 void dense_solve(const T* Ainv, int n, const T* b, i64 bs, T* x, i64 xs, i64 nn, int nc, int nrhs,
                  const int* active, cudaStream_t s) {
   (void)nn;
   (void)nc;
-  k_dense_solve<T><<<dim3(nblocks(n, 128), nrhs), 128, 0, s>>>(Ainv, n, b, bs, x, xs, active);
+  note_launch(), k_dense_solve<T><<<dim3(nblocks(n, 128), nrhs), 128, 0, s>>>(Ainv, n, b, bs, x, xs, active);
 }
 
 #define INST_NC(T, NC)                                                                              \
