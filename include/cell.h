@@ -200,6 +200,24 @@ int cell_get_rho(cell_handle* h, double* out);
  * Schur complement S0 for the material and grid of d (d->input unused). */
 int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]);
 
+/* Homogenised tensors like cell_homogenise, but from fields the caller passes
+ * and without allocating any device memory (the paper has no counterpart; this
+ * serves callers that cannot allocate at that point, e.g. code being captured
+ * into a CUDA graph or running under an allocator that forbids cudaMalloc).
+ * d gives the grid, material and stream (d->input and d->opt are unused).
+ * rho: N element scales; bhat, y, rhat: 9 FP64 cell vectors each (9*4*N
+ * values): the right-hand sides as from cell_rhs, the solutions as from
+ * cell_get_solution, and the residuals bhat - Ahat y; all DEVICE pointers.
+ * Block partial sums live in one fixed device array inside the library
+ * (672 KB, held on every GPU that loads it), shared by all calls: calls that
+ * overlap on the GPU race and must be ordered (e.g. issued on one stream).
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Synchronises d->stream.
+ * CELL_EINVAL for null pointers, sizes < 2, or more than 4,194,304 nodes. */
+int cell_homogenise_noalloc(const cell_desc* d, const double* rho, const double* bhat,
+                            const double* y, const double* rhat, double CH[36], double eH[18],
+                            double kH[9]);
+
 /* Number of kernels this library has launched in the calling process so far
  * (all handles, all threads); lets a caller count the launches of a region. */
 long long cell_launch_count(void);

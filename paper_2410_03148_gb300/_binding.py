@@ -25,8 +25,8 @@ CELL_F32, CELL_F64 = 0, 1
 EXPORTS = [
     "cell_default_options", "cell_setup", "cell_solve", "cell_homogenise", "cell_sensitivity",
     "cell_dh", "cell_get_solution", "cell_apply", "cell_rhs", "cell_get_rho",
-    "cell_element_matrices", "cell_launch_count", "cell_destroy", "cell_status_str",
-    "cell_last_error",
+    "cell_element_matrices", "cell_homogenise_noalloc", "cell_launch_count", "cell_destroy",
+    "cell_status_str", "cell_last_error",
 ]
 
 
@@ -99,6 +99,8 @@ def load(path: str = LIB_PATH):
     lib.cell_destroy.restype = None
     lib.cell_status_str.argtypes = [C.c_int]
     lib.cell_status_str.restype = C.c_char_p
+    lib.cell_homogenise_noalloc.argtypes = [C.POINTER(cell_desc), P, P, P, P, D, D, D]
+    lib.cell_homogenise_noalloc.restype = C.c_int
     lib.cell_launch_count.argtypes = []
     lib.cell_launch_count.restype = C.c_longlong
     lib.cell_last_error.argtypes = []
@@ -231,6 +233,18 @@ def cell_element_matrices(desc: cell_desc):
         C.byref(desc), K0.ctypes.data_as(C.POINTER(C.c_double)),
         S0.ctypes.data_as(C.POINTER(C.c_double))))
     return K0.reshape(32, 32), S0.reshape(8, 8)
+
+
+def cell_homogenise_noalloc(desc: cell_desc, rho_ptr: int, b_ptr: int, y_ptr: int, r_ptr: int):
+    """Homogenised tensors from caller-provided device fields, without any
+    device allocation (see include/cell.h)."""
+    CH, eH, kH = np.zeros(36), np.zeros(18), np.zeros(9)
+    s = load().cell_homogenise_noalloc(
+        C.byref(desc), C.c_void_p(rho_ptr), C.c_void_p(b_ptr), C.c_void_p(y_ptr), C.c_void_p(r_ptr),
+        CH.ctypes.data_as(C.POINTER(C.c_double)), eH.ctypes.data_as(C.POINTER(C.c_double)),
+        kH.ctypes.data_as(C.POINTER(C.c_double)))
+    _check("cell_homogenise_noalloc", s)
+    return CH.reshape(6, 6), eH.reshape(3, 6), kH.reshape(3, 3)
 
 
 def cell_launch_count() -> int:
