@@ -792,7 +792,7 @@ void cell_default_options(cell_options* o) {
   o->vcycles_u = 1;
   o->vcycles_phi = 1;
   o->cheb_degree = 3;
-  o->cheb_lo = 0.05;
+  o->cheb_lo = 0.03;
   o->cheb_hi = 1.0;
   o->schur_shift = 1e-10;
   o->coarse_dofs = 200;
