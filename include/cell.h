@@ -68,7 +68,11 @@ typedef enum cell_input_kind {
   CELL_INPUT_PHI = 1    /* input = nodal level-set values; rho from §2.6 smoothing */
 } cell_input_kind;
 
-typedef enum cell_dtype { CELL_F32 = 0, CELL_F64 = 1 } cell_dtype;
+typedef enum cell_dtype {
+  CELL_F32 = 0,
+  CELL_F64 = 1,
+  CELL_F64_DF = 2   /* FP64 data, arithmetic in FP32 pairs (cell_apply only) */
+} cell_dtype;
 
 typedef struct cell_options {
   double tol;          /* stop when ||r_I||_2 <= tol * ||b_I||_2 for every load I
@@ -148,6 +152,13 @@ void cell_default_options(cell_options* opt);
  * unknown enums or null pointers; CELL_ENOMEM; CELL_ECUDA. */
 int cell_setup(const cell_desc* d, cell_handle** out);
 
+/* Replace the design of an existing handle (same grid, material, input kind
+ * and dtype as at cell_setup; input is a DEVICE pointer of nx*ny*nz values)
+ * and rebuild everything that depends on it (rho_e, multigrid numerics)
+ * without allocating: the repeated S1 of an optimisation loop.  Invalidates
+ * the previous solution.  CELL_EINVAL for null pointers or invalid rho. */
+int cell_update(cell_handle* h, const void* input);
+
 /* Solve the selected cell problems (§2.2) for the design of the handle:
  * assemble b = -sum_e rho_e P_e^T K0 Zbar_e (negated potential rows, the
  * nonsymmetric form of Eq. (sym-piezo)), run right-preconditioned SCP-GMRES
@@ -185,7 +196,11 @@ int cell_get_solution(cell_handle* h, double* out);
 
 /* y = Ahat x for nrhs cell vectors (device pointers, dtype CELL_F32 or
  * CELL_F64): the assembled nonsymmetric operator of Eq. (sym-piezo) second
- * form, sum_e rho_e P_e^T K0 P_e x with the potential rows negated. */
+ * form, sum_e rho_e P_e^T K0 P_e x with the potential rows negated.
+ * CELL_F64_DF: FP64 vectors (nrhs <= 9), evaluated with the FP32 double-float
+ * kernel that the mixed solver uses for its FP64-grade residuals (error-free
+ * FMA products, TwoSum accumulation); it overwrites the handle's internal
+ * split-iterate buffers, so call it only between solves. */
 int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype);
 
 /* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as

@@ -19,11 +19,11 @@ LIB_PATH = os.path.join(HERE, "libcell.so")
 CELL_OK, CELL_EINVAL, CELL_ENOMEM, CELL_ENOTCONV, CELL_ETIMEOUT, CELL_ECUDA, CELL_ESTATE = range(7)
 CELL_FP64, CELL_MIXED_FP32 = 0, 1
 CELL_INPUT_RHO, CELL_INPUT_PHI = 0, 1
-CELL_F32, CELL_F64 = 0, 1
+CELL_F32, CELL_F64, CELL_F64_DF = 0, 1, 2
 
 # every symbol include/cell.h declares
 EXPORTS = [
-    "cell_default_options", "cell_setup", "cell_solve", "cell_homogenise", "cell_sensitivity",
+    "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_homogenise", "cell_sensitivity",
     "cell_dh", "cell_get_solution", "cell_apply", "cell_rhs", "cell_get_rho",
     "cell_element_matrices", "cell_homogenise_noalloc", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
@@ -86,6 +86,7 @@ def load(path: str = LIB_PATH):
     lib.cell_default_options.argtypes = [C.POINTER(cell_options)]
     lib.cell_default_options.restype = None
     lib.cell_setup.argtypes = [C.POINTER(cell_desc), C.POINTER(P)]
+    lib.cell_update.argtypes = [P, P]
     lib.cell_solve.argtypes = [P, C.POINTER(cell_stats)]
     lib.cell_homogenise.argtypes = [P, D, D, D]
     lib.cell_sensitivity.argtypes = [P, D, D, D, P, C.c_int]
@@ -105,7 +106,7 @@ def load(path: str = LIB_PATH):
     lib.cell_launch_count.restype = C.c_longlong
     lib.cell_last_error.argtypes = []
     lib.cell_last_error.restype = C.c_char_p
-    for name in ("cell_setup", "cell_solve", "cell_homogenise", "cell_sensitivity", "cell_dh",
+    for name in ("cell_setup", "cell_update", "cell_solve", "cell_homogenise", "cell_sensitivity", "cell_dh",
                  "cell_get_solution", "cell_apply", "cell_rhs", "cell_get_rho",
                  "cell_element_matrices"):
         getattr(lib, name).restype = C.c_int
@@ -169,6 +170,10 @@ def cell_setup(desc: cell_desc):
     h = C.c_void_p()
     _check("cell_setup", load().cell_setup(C.byref(desc), C.byref(h)))
     return h
+
+
+def cell_update(h, input_ptr: int):
+    _check("cell_update", load().cell_update(h, C.c_void_p(input_ptr)))
 
 
 def cell_solve(h, allow_notconv=False):

@@ -29,6 +29,7 @@ class Cell:
         B.load()
         self.device = design.device
         self.shape = tuple(design.shape)
+        self.dtype = design.dtype
         nz, ny, nx = self.shape
         design = design.contiguous()
         Cm, em, km = material
@@ -43,6 +44,13 @@ class Cell:
         self.stats = None
 
     # -- hot path --------------------------------------------------------------
+    def update(self, design: torch.Tensor):
+        """Swap in a new design of the same shape/kind/dtype (no reallocation)."""
+        if tuple(design.shape) != self.shape or not design.is_cuda or design.dtype != self.dtype:
+            raise ValueError("design must be a CUDA tensor of the handle's shape and dtype")
+        design = design.contiguous()
+        B.cell_update(self._h, design.data_ptr())
+
     def solve(self, allow_notconv: bool = False):
         status, st = B.cell_solve(self._h, allow_notconv)
         self.stats = {

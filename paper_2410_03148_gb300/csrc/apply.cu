@@ -75,21 +75,36 @@ __device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const Nod
 }
 
 // Fixed-matrix operator, FP32: the 27 neighbours are preloaded into registers
-// and every coefficient index is a compile-time constant.
+// and every coefficient index is a compile-time constant.  Neighbour offsets
+// are 32-bit and each component plane has its own base pointer, so a load is
+// one address multiply-add.
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
   const int r = blockIdx.z;
   if (a.active && !a.active[r]) return;
+  const int nx = a.nx, ny = a.ny;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nx * ny) return;
+  const int j = p / nx;
+  const int i = p - j * nx;
+  const int k = blockIdx.y;
+  const int nxy = nx * ny;
+  const int xo[3] = {i == 0 ? nx - 1 : i - 1, i, i == nx - 1 ? 0 : i + 1};
+  const int yo[3] = {(j == 0 ? ny - 1 : j - 1) * nx, j * nx, (j == ny - 1 ? 0 : j + 1) * nx};
+  const int zo[3] = {(k == 0 ? a.nz - 1 : k - 1) * nxy, k * nxy, (k == a.nz - 1 ? 0 : k + 1) * nxy};
   NodeIdx t;
-  if (!node_index(a.nx, a.ny, a.nz, t)) return;
-  const T* X = a.x + r * a.xs;
+  t.nn = (i64)nxy * a.nz;
+  t.n = (i64)k * nxy + p;
+  const T* X[NCI];
+#pragma unroll
+  for (int d = 0; d < NCI; ++d) X[d] = a.x + r * a.xs + d * t.nn;
   T xs[27][NCI];
 #pragma unroll
   for (int q = 0; q < 27; ++q) {
-    const i64 m = t.xo[q % 3] + t.yo[(q / 3) % 3] + t.zo[q / 9];
+    const int m = xo[q % 3] + yo[(q / 3) % 3] + zo[q / 9];
 #pragma unroll
-    for (int d = 0; d < NCI; ++d) xs[q][d] = __ldg(X + d * t.nn + m);
+    for (int d = 0; d < NCI; ++d) xs[q][d] = __ldg(X[d] + m);
   }
   T acc[NCO];
 #pragma unroll
@@ -98,7 +113,7 @@ k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM>
   for (int e = 0; e < 8; ++e) {
     const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
     const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
-    const T w = __ldg(a.rho + t.xo[ex] + t.yo[ey] + t.zo[ez]);
+    const T w = __ldg(a.rho + (xo[ex] + yo[ey] + zo[ez]));
     T tl[NCO];
 #pragma unroll
     for (int c = 0; c < NCO; ++c) tl[c] = T(0);
@@ -234,6 +249,181 @@ __global__ void __launch_bounds__(kBlock) k_apply_elem(const ApplyArgs<T> a, int
   }
 }
 
+// Assembled block stencil on a coarse level: y_n = sum_q S_n[q] x_{n+q} over the
+// 27 neighbours q (offsets in {-1,0,1}^3, q = dx + 3 dy + 9 dz).  One thread per
+// node and group of RG loads; the node's stencil row (27 NC x NC blocks) is
+// read once per group with coalesced loads.
+template <typename T, int NC, int RG, int MODE>
+__global__ void __launch_bounds__(kBlock) k_apply_st(const ApplyArgs<T> a, int nrhs) {
+  NodeIdx t;
+  if (!node_index(a.nx, a.ny, a.nz, t)) return;
+  const int r0 = blockIdx.z * RG;
+  bool on[RG];
+  bool any = false;
+#pragma unroll
+  for (int g = 0; g < RG; ++g) {
+    on[g] = (r0 + g < nrhs) && !(a.active && !a.active[r0 + g]);
+    any = any || on[g];
+  }
+  if (!any) return;
+  T acc[RG][NC], dold[RG][NC];
+#pragma unroll
+  for (int g = 0; g < RG; ++g)
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[g][c] = dold[g][c] = T(0);
+  const T* S = a.st + t.n;
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int m = (int)(t.xo[q % 3] + t.yo[(q / 3) % 3] + t.zo[q / 9]);
+    T sb[NC][NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+      for (int d = 0; d < NC; ++d) sb[c][d] = __ldg(S + (i64)((q * NC + c) * NC + d) * t.nn);
+#pragma unroll
+    for (int g = 0; g < RG; ++g) {
+      if (!on[g]) continue;
+      const T* X = a.x + (r0 + g) * a.xs;
+#pragma unroll
+      for (int d = 0; d < NC; ++d) {
+        const T xv = __ldg(X + d * t.nn + m);
+        if (q == 13) dold[g][d] = xv;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) acc[g][c] = fma(sb[c][d], xv, acc[g][c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < RG; ++g) {
+    if (!on[g]) continue;
+    epilogue<T, NC, MODE>(a, r0 + g, t, acc[g], dold[g]);
+  }
+}
+
+// One thread per (node, output component c): accumulate the element blocks of
+// the 8 elements around the node into its 27 neighbour blocks.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kBlock) k_stencil(const T* __restrict__ ke, T* __restrict__ st,
+                                                   int nx, int ny, int nz) {
+  NodeIdx t;
+  if (!node_index(nx, ny, nz, t)) return;
+  const int c = blockIdx.z;
+  constexpr int R = 8 * NC;
+  T acc[27][NC];
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+#pragma unroll
+    for (int d = 0; d < NC; ++d) acc[q][d] = T(0);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+    const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+    const i64 el = t.xo[ex] + t.yo[ey] + t.zo[ez];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int q = (ex + (b & 1)) + 3 * (ey + ((b >> 1) & 1)) + 9 * (ez + (b >> 2));
+#pragma unroll
+      for (int d = 0; d < NC; ++d)
+        acc[q][d] += __ldg(ke + (i64)((la * NC + c) * R + b * NC + d) * t.nn + el);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 27; ++q)
+#pragma unroll
+    for (int d = 0; d < NC; ++d) st[(i64)((q * NC + c) * NC + d) * t.nn + t.n] = acc[q][d];
+}
+
+// Double-float helpers: exact product and sum error transformations.
+__device__ __forceinline__ void two_sum(float& s, float& lo, float p) {
+  const float t = s + p;
+  const float bb = t - s;
+  lo += (s - (t - bb)) + (p - bb);
+  s = t;
+}
+
+// r = b - Ahat x with FP64-grade accuracy from FP32 arithmetic only.
+__global__ void __launch_bounds__(kBlock)
+k_resid_df(const float* __restrict__ xh, const float* __restrict__ xl, i64 xs,
+           const double* __restrict__ b, i64 bs, double* __restrict__ r, i64 rs,
+           const float* __restrict__ rho_h, const float* __restrict__ rho_l,
+           const __grid_constant__ DFMat M, int nx, int ny, int nz, const int* active) {
+  const int q = blockIdx.z;
+  if (active && !active[q]) return;
+  NodeIdx t;
+  if (!node_index(nx, ny, nz, t)) return;
+  const float* XH = xh + q * xs;
+  const float* XL = xl + q * xs;
+  float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+    const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+    const i64 el = t.xo[ex] + t.yo[ey] + t.zo[ez];
+    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int bn = 0; bn < 8; ++bn) {
+      const i64 m = t.xo[ex + (bn & 1)] + t.yo[ey + ((bn >> 1) & 1)] + t.zo[ez + (bn >> 2)];
+#pragma unroll
+      for (int d = 0; d < 4; ++d) {
+        const float vh = __ldg(XH + d * t.nn + m), vl = __ldg(XL + d * t.nn + m);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int k = (la * 4 + c) * 32 + bn * 4 + d;
+          const float p = M.kh[k] * vh;
+          const float pe = fmaf(M.kh[k], vh, -p);
+          two_sum(sh[c], sl[c], p);
+          sl[c] = fmaf(M.kh[k], vl, fmaf(M.kl[k], vh, sl[c] + pe));
+        }
+      }
+    }
+    const float wh = __ldg(rho_h + el), wl = __ldg(rho_l + el);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const float p = sh[c] * wh;
+      const float pe = fmaf(sh[c], wh, -p);
+      two_sum(ah[c], al[c], p);
+      al[c] = fmaf(sh[c], wl, fmaf(sl[c], wh, al[c] + pe));
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    double v = (double)ah[c] + (double)al[c];
+    if (c == 3) v = -v;
+    const i64 o = (i64)c * t.nn + t.n;
+    r[q * rs + o] = b ? b[q * bs + o] - v : v;
+  }
+}
+
+__global__ void k_axpy_split_f(double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
+                               i64 xs, const float* __restrict__ d, i64 ds, i64 len,
+                               const double* __restrict__ sc, const int* active) {
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  const double f = sc[q];
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x) {
+    const double v = x[q * xs + k] + f * (double)d[q * ds + k];
+    x[q * xs + k] = v;
+    const float h = (float)v;
+    xh[q * xs + k] = h;
+    xl[q * xs + k] = (float)(v - (double)h);
+  }
+}
+
+__global__ void k_axpy_split_d(double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
+                               i64 xs, const double* __restrict__ d, i64 ds, i64 len,
+                               const double* __restrict__ sc, const int* active) {
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  const double f = sc[q];
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x) {
+    const double v = x[q * xs + k] + f * d[q * ds + k];
+    x[q * xs + k] = v;
+    const float h = (float)v;
+    xh[q * xs + k] = h;
+    xl[q * xs + k] = (float)(v - (double)h);
+  }
+}
+
 template <typename T>
 inline dim3 grid_for(const ApplyArgs<T>& a, int nrhs) {
   const int plane = a.nx * a.ny;
@@ -301,13 +491,86 @@ void apply_elem(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
   else launch_elem<T, NC, 1>(a, mode, nrhs, s);
 }
 
+template <typename T, int NC, int RG>
+void launch_st(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
+  const dim3 g = grid_for(a, (nrhs + RG - 1) / RG);
+  switch (mode) {
+    case AM_LINEAR: note_launch(), k_apply_st<T, NC, RG, AM_LINEAR><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    case AM_CHEB: note_launch(), k_apply_st<T, NC, RG, AM_CHEB><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    case AM_CHEB_LAST: note_launch(), k_apply_st<T, NC, RG, AM_CHEB_LAST><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    default: note_launch(), k_apply_st<T, NC, RG, AM_RESID_CHEB0><<<g, kBlock, 0, s>>>(a, nrhs); break;
+  }
+}
+
+template <typename T, int NC>
+void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
+  const long long nn = (long long)a.nx * a.ny * a.nz;
+  if (nn >= 32768) launch_st<T, NC, 3>(a, mode, nrhs, s);
+  else launch_st<T, NC, 1>(a, mode, nrhs, s);
+}
+
+template <typename T, int NC>
+void stencil_from_elem(const T* ke, T* st, int nx, int ny, int nz, cudaStream_t s) {
+  ApplyArgs<T> a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  note_launch(), k_stencil<T, NC><<<grid_for(a, NC), kBlock, 0, s>>>(ke, st, nx, ny, nz);
+}
+
+void resid_df(const float* xh, const float* xl, i64 xs, const double* b, i64 bs, double* r, i64 rs,
+              const float* rho_h, const float* rho_l, const DFMat& M, int nx, int ny, int nz,
+              int nrhs, const int* active, cudaStream_t s) {
+  ApplyArgs<float> a{};
+  a.nx = nx;
+  a.ny = ny;
+  a.nz = nz;
+  note_launch(), k_resid_df<<<grid_for(a, nrhs), kBlock, 0, s>>>(xh, xl, xs, b, bs, r, rs, rho_h, rho_l, M,
+                                                                  nx, ny, nz, active);
+}
+
+__global__ void k_split(const double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
+                        i64 n) {
+  for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (i64)gridDim.x * blockDim.x) {
+    const double v = x[k];
+    const float h = (float)v;
+    xh[k] = h;
+    xl[k] = (float)(v - (double)h);
+  }
+}
+
+void split_f64(const double* x, float* xh, float* xl, i64 n, cudaStream_t s) {
+  i64 blocks = (n + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  note_launch(), k_split<<<(unsigned)blocks, 256, 0, s>>>(x, xh, xl, n);
+}
+
+template <typename T>
+void axpy_split(double* x, float* xh, float* xl, i64 xs, const T* d, i64 ds, i64 len,
+                const double* sc, int nrhs, const int* active, cudaStream_t s) {
+  i64 blocks = (len + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if constexpr (sizeof(T) == 4)
+    note_launch(), k_axpy_split_f<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(x, xh, xl, xs, d, ds, len, sc, active);
+  else
+    note_launch(), k_axpy_split_d<<<dim3((unsigned)blocks, nrhs), 256, 0, s>>>(x, xh, xl, xs, d, ds, len, sc, active);
+}
+template void axpy_split<float>(double*, float*, float*, i64, const float*, i64, i64, const double*,
+                                int, const int*, cudaStream_t);
+template void axpy_split<double>(double*, float*, float*, i64, const double*, i64, i64,
+                                 const double*, int, const int*, cudaStream_t);
+
 #define INST(T)                                                                                   \
   template void apply_full<T>(const ApplyArgs<T>&, const FixedMat<T, 4>&, int, int, cudaStream_t); \
   template void apply_uu<T>(const ApplyArgs<T>&, const FixedMat<T, 4>&, int, int, cudaStream_t);   \
   template void apply_pu<T>(const ApplyArgs<T>&, const FixedMat<T, 4>&, int, cudaStream_t);        \
   template void apply_ss<T>(const ApplyArgs<T>&, const FixedMat<T, 1>&, int, int, cudaStream_t);   \
   template void apply_elem<T, 1>(const ApplyArgs<T>&, int, int, cudaStream_t);                     \
-  template void apply_elem<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t);
+  template void apply_elem<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t);                     \
+  template void apply_stencil<T, 1>(const ApplyArgs<T>&, int, int, cudaStream_t);                  \
+  template void apply_stencil<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t);                  \
+  template void stencil_from_elem<T, 1>(const T*, T*, int, int, int, cudaStream_t);                \
+  template void stencil_from_elem<T, 3>(const T*, T*, int, int, int, cudaStream_t);
 INST(float)
 INST(double)
 #undef INST

@@ -127,6 +127,7 @@ struct Level {
   int nx = 0, ny = 0, nz = 0;
   i64 nn = 0;
   T* ke = nullptr;       // per-element Galerkin matrices (levels >= 1), SoA
+  T* st = nullptr;       // assembled 27-point block stencil (levels >= 1), SoA
   T* dinv = nullptr;     // [NC][nn]
   double lmax = 1.0;
   T *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *d2 = nullptr;  // [9][NC][nn]
@@ -141,6 +142,8 @@ struct BlockMG {
   std::vector<Level<T>> lv;
   T* fixedm = nullptr;   // device copy of the level-0 element block ((8nc)^2)
   std::vector<double> fixed_host;
+  std::vector<T> dense_host;   // staging of the coarsest inverse (kept alive for the async copy)
+  unsigned int* lbits = nullptr;  // per-level lambda_max bounds (float bits)
 };
 
 template <typename T>
@@ -177,6 +180,10 @@ struct cell_handle {
   double* rho64 = nullptr;
   double* K0dev = nullptr;
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr;
+  // mixed path: x64 as FP32 pairs and rho's low part, for the double-float residual
+  float *xh = nullptr, *xl = nullptr, *rho_l = nullptr, *rho_tmp = nullptr;
+  int* bad = nullptr;
+  cell::DFMat DF;
   double *partial = nullptr, *red = nullptr, *red2 = nullptr;
   int nblk = 0;
   // per-load magnitude of the element contributions, sqrt(sum rho_e^2) |K0 Zbar^I|:
@@ -225,8 +232,8 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
     if (NC == 3) cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
     else cell::apply_ss<T>(a, K.S0, mode, 9, h->st);
   } else {
-    a.ke = L.ke;
-    cell::apply_elem<T, NC>(a, mode, 9, h->st);
+    a.st = L.st;
+    cell::apply_stencil<T, NC>(a, mode, 9, h->st);
   }
   h->prof.end(l > 0 ? CELL_PROF_COARSE : (NC == 3 ? CELL_PROF_ELASTIC0 : CELL_PROF_SCHUR0), ip, h->st);
 }
@@ -266,8 +273,9 @@ int assemble_dense(cell_handle* h, BlockMG<T>& mg, int l, std::vector<double>& A
   return CELL_OK;
 }
 
+// Structure and allocations of a block's multigrid hierarchy (once per handle).
 template <typename T, int NC>
-int build_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
+int alloc_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
   const cell_options& o = h->d.opt;
   const int R = 8 * NC;
   mg.nc = NC;
@@ -299,27 +307,13 @@ int build_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
     mg.lv.push_back(C);
   }
   const int nl = (int)mg.lv.size();
-  unsigned int* lbits = nullptr;
-  CKS(h->arena.alloc(&lbits, 1));
+  CKS(h->arena.alloc(&mg.lbits, nl));
   for (int l = 0; l < nl; ++l) {
     Level<T>& L = mg.lv[l];
     CKS(h->arena.alloc(&L.dinv, NC * L.nn));
     if (l > 0) {
-      Level<T>& F = mg.lv[l - 1];
       CKS(h->arena.alloc(&L.ke, (size_t)R * R * L.nn));
-      if (l == 1) cell::galerkin<T, NC>(mg.fixedm, rho_of<T>(h), nullptr, L.ke, L.nx, L.ny, L.nz, h->st);
-      else cell::galerkin<T, NC>(nullptr, nullptr, F.ke, L.ke, L.nx, L.ny, L.nz, h->st);
-      cell::diag_inv<T, NC>(nullptr, nullptr, L.ke, L.dinv, L.nx, L.ny, L.nz, h->st);
-      CK(cudaMemsetAsync(lbits, 0, sizeof(unsigned), h->st));
-      cell::elem_lmax<T, NC>(L.ke, L.nn, lbits, h->st);
-      unsigned bits = 0;
-      CK(cudaMemcpyAsync(&bits, lbits, sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
-      CK(cudaStreamSynchronize(h->st));
-      float lf;
-      std::memcpy(&lf, &bits, sizeof(float));
-      L.lmax = lf > 0 ? (double)lf : 1.0;
-    } else {
-      cell::diag_inv<T, NC>(mg.fixedm, rho_of<T>(h), nullptr, L.dinv, L.nx, L.ny, L.nz, h->st);
+      CKS(h->arena.alloc(&L.st, (size_t)27 * NC * NC * L.nn));
     }
     const size_t wn = (size_t)9 * NC * L.nn;
     if (l > 0) {
@@ -334,8 +328,39 @@ int build_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
   Lc.coarsest = true;
   const i64 n = NC * Lc.nn;
   if (n <= 3000) {
+    CKS(h->arena.alloc(&Lc.dense, (size_t)n * n));
+    Lc.ndense = (int)n;
+  }
+  return CELL_OK;
+}
+
+// Numerics of the hierarchy for the handle's current rho (every design):
+// Galerkin coarse element matrices, stencils, Jacobi diagonals, Chebyshev
+// bounds and the coarsest regularised inverse.
+template <typename T, int NC>
+int fill_mg(cell_handle* h, BlockMG<T>& mg) {
+  const int nl = (int)mg.lv.size();
+  CK(cudaMemsetAsync(mg.lbits, 0, nl * sizeof(unsigned), h->st));
+  for (int l = 0; l < nl; ++l) {
+    Level<T>& L = mg.lv[l];
+    if (l > 0) {
+      Level<T>& F = mg.lv[l - 1];
+      if (l == 1) cell::galerkin<T, NC>(mg.fixedm, rho_of<T>(h), nullptr, L.ke, L.nx, L.ny, L.nz, h->st);
+      else cell::galerkin<T, NC>(nullptr, nullptr, F.ke, L.ke, L.nx, L.ny, L.nz, h->st);
+      cell::diag_inv<T, NC>(nullptr, nullptr, L.ke, L.dinv, L.nx, L.ny, L.nz, h->st);
+      cell::stencil_from_elem<T, NC>(L.ke, L.st, L.nx, L.ny, L.nz, h->st);
+      cell::elem_lmax<T, NC>(L.ke, L.nn, mg.lbits + l, h->st);
+    } else {
+      cell::diag_inv<T, NC>(mg.fixedm, rho_of<T>(h), nullptr, L.dinv, L.nx, L.ny, L.nz, h->st);
+    }
+  }
+  std::vector<unsigned> bits(nl, 0u);
+  CK(cudaMemcpyAsync(bits.data(), mg.lbits, nl * sizeof(unsigned), cudaMemcpyDeviceToHost, h->st));
+  Level<T>& Lc = mg.lv.back();
+  if (Lc.dense) {
+    const i64 n = Lc.ndense;
     std::vector<double> A;
-    CKS((assemble_dense<T, NC>(h, mg, nl - 1, A)));
+    CKS((assemble_dense<T, NC>(h, mg, nl - 1, A)));  // synchronises the stream
     // regularise the null space (componentwise constants) and invert
     double tr = 0.0;
     for (i64 i = 0; i < n; ++i) tr += A[(size_t)i * n + i];
@@ -347,12 +372,16 @@ int build_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
       set_error("coarsest multigrid level is not positive definite (rho must be > 0)");
       return CELL_EINVAL;
     }
-    std::vector<T> At(A.size());
-    for (size_t i = 0; i < A.size(); ++i) At[i] = (T)A[i];
-    CKS(h->arena.alloc(&Lc.dense, At.size()));
-    CK(cudaMemcpyAsync(Lc.dense, At.data(), At.size() * sizeof(T), cudaMemcpyHostToDevice, h->st));
-    Lc.ndense = (int)n;
-    CK(cudaStreamSynchronize(h->st));
+    mg.dense_host.resize(A.size());
+    for (size_t i = 0; i < A.size(); ++i) mg.dense_host[i] = (T)A[i];
+    CK(cudaMemcpyAsync(Lc.dense, mg.dense_host.data(), mg.dense_host.size() * sizeof(T),
+                       cudaMemcpyHostToDevice, h->st));
+  }
+  CK(cudaStreamSynchronize(h->st));
+  for (int l = 1; l < nl; ++l) {
+    float lf;
+    std::memcpy(&lf, &bits[l], sizeof(float));
+    mg.lv[l].lmax = lf > 0 ? (double)lf : 1.0;
   }
   return CELL_OK;
 }
@@ -499,8 +528,16 @@ int setup_krylov(cell_handle* h) {
     for (int c = 0; c < 3; ++c)
       for (int b = 0; b < 8; ++b)
         for (int d = 0; d < 3; ++d) Auu[(a * 3 + c) * 24 + b * 3 + d] = h->K0[(4 * a + c) * 32 + 4 * b + d];
-  CKS((build_mg<T, 3>(h, K.mgu, Auu.data())));
-  CKS((build_mg<T, 1>(h, K.mgp, h->S0)));
+  CKS((alloc_mg<T, 3>(h, K.mgu, Auu.data())));
+  CKS((alloc_mg<T, 1>(h, K.mgp, h->S0)));
+  return CELL_OK;
+}
+
+template <typename T>
+int fill_krylov(cell_handle* h) {
+  Krylov<T>& K = kry<T>(h);
+  CKS((fill_mg<T, 3>(h, K.mgu)));
+  CKS((fill_mg<T, 1>(h, K.mgp)));
   return CELL_OK;
 }
 
@@ -565,7 +602,10 @@ int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
   cell::backsolve(h->H, h->g, h->kcount, m, h->ybuf, 9, h->ranmask, s);
   cell::lincomb<T>(K.V, vstride, len, h->ybuf, h->kcount, kNvMax, K.u, len, len, 9, h->ranmask, s);
   precond<T>(h, K.u, K.z, h->ranmask);
-  cell::axpy_f64<T>(h->x64, len, K.z, len, len, h->ones, 9, h->ranmask, s);
+  if constexpr (sizeof(T) == 4)
+    cell::axpy_split<T>(h->x64, h->xh, h->xl, len, K.z, len, len, h->ones, 9, h->ranmask, s);
+  else
+    cell::axpy_f64<T>(h->x64, len, K.z, len, len, h->ones, 9, h->ranmask, s);
   int kc[9];
   CK(cudaMemcpyAsync(kc, h->kcount, sizeof(kc), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -586,6 +626,49 @@ int check_options(const cell_options& o) {
   if (!(o.cheb_lo > 0.0 && o.cheb_lo < 1.0) || !(o.cheb_hi > 0.0)) return CELL_EINVAL;
   if (!(o.schur_shift >= 0.0) || o.coarse_dofs < 1) return CELL_EINVAL;
   if ((o.load_mask & 0x1FF) == 0 || (o.load_mask & ~0x1FF)) return CELL_EINVAL;
+  return CELL_OK;
+}
+
+// Map a design (rho or level set, device pointer of the kind/dtype given at
+// set-up) into the handle: rho_e on the device, its FP32 split, the rounding
+// floor of the loads, and the multigrid numerics.  No allocation.
+int load_design(cell_handle* h, const void* input) {
+  const cell_desc* d = &h->d;
+  const i64 nn = h->nn;
+  CK(cudaMemsetAsync(h->bad, 0, sizeof(int), h->st));
+  if (d->input_kind == CELL_INPUT_PHI) {
+    const double eta = d->eta > 0 ? d->eta : 2.0 * std::max(h->h[0], std::max(h->h[1], h->h[2]));
+    if (d->input_dtype == CELL_F32)
+      cell::ersatz<float>(static_cast<const float*>(input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
+    else
+      cell::ersatz<double>(static_cast<const double*>(input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
+  } else {
+    if (d->input_dtype == CELL_F32)
+      cell::rho_copy<float>(static_cast<const float*>(input), nn, h->rho32, h->rho64, h->bad, h->st);
+    else
+      cell::rho_copy<double>(static_cast<const double*>(input), nn, h->rho32, h->rho64, h->bad, h->st);
+  }
+  // rho_l = fp32(rho64 - rho32)
+  cell::split_f64(h->rho64, h->rho_tmp, h->rho_l, nn, h->st);
+  double srho2 = 0.0;
+  int nbad = 0;
+  cell::sum_reduce(h->rho64, nn, h->partial, h->nblk, h->red, h->st, 1);
+  CK(cudaMemcpyAsync(&srho2, h->red, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaMemcpyAsync(&nbad, h->bad, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (nbad) {
+    set_error("rho input has non-positive or non-finite values");
+    return CELL_EINVAL;
+  }
+  for (int I = 0; I < 9; ++I) {
+    double f2 = 0.0;
+    for (int a = 0; a < 32; ++a) f2 += h->F[a * 9 + I] * h->F[a * 9 + I];
+    h->bfloor[I] = 1e-13 * std::sqrt(srho2 * f2);
+  }
+  if (d->opt.precision == CELL_MIXED_FP32) CKS(fill_krylov<float>(h));
+  else CKS(fill_krylov<double>(h));
+  h->solved = false;
+  CK(cudaGetLastError());
   return CELL_OK;
 }
 
@@ -620,39 +703,30 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
       for (int a = 0; a < 32; ++a) s += h->Z[a * 9 + I] * h->F[a * 9 + J];
       h->H0e[I * 9 + J] = s;
     }
+  // the FP64 operator serves the refinement residual of the FP64 path
+  std::memcpy(h->kd.K0.k, h->K0, sizeof(h->kd.K0.k));
+  std::memcpy(h->kd.S0.k, h->S0, sizeof(h->kd.S0.k));
+  for (int i = 0; i < 1024; ++i) {
+    h->DF.kh[i] = (float)h->K0[i];
+    h->DF.kl[i] = (float)(h->K0[i] - (double)h->DF.kh[i]);
+  }
+  // every device allocation of the handle happens here
   const i64 nn = h->nn;
+  const i64 len = 4 * nn;
   Arena& A = h->arena;
   CKS(A.alloc(&h->rho32, nn));
   CKS(A.alloc(&h->rho64, nn));
+  CKS(A.alloc(&h->rho_l, nn));
+  CKS(A.alloc(&h->rho_tmp, nn));
+  CKS(A.alloc(&h->bad, 1));
   CKS(A.alloc(&h->K0dev, 1024));
   CK(cudaMemcpyAsync(h->K0dev, h->K0, 1024 * sizeof(double), cudaMemcpyHostToDevice, h->st));
-  int* bad = nullptr;
-  CKS(A.alloc(&bad, 1));
-  CK(cudaMemsetAsync(bad, 0, sizeof(int), h->st));
-  if (d->input_kind == CELL_INPUT_PHI) {
-    const double eta = d->eta > 0 ? d->eta : 2.0 * std::max(h->h[0], std::max(h->h[1], h->h[2]));
-    if (d->input_dtype == CELL_F32)
-      cell::ersatz<float>(static_cast<const float*>(d->input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
-    else
-      cell::ersatz<double>(static_cast<const double*>(d->input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
-  } else {
-    if (d->input_dtype == CELL_F32)
-      cell::rho_copy<float>(static_cast<const float*>(d->input), nn, h->rho32, h->rho64, bad, h->st);
-    else
-      cell::rho_copy<double>(static_cast<const double*>(d->input), nn, h->rho32, h->rho64, bad, h->st);
-  }
-  int nbad = 0;
-  CK(cudaMemcpyAsync(&nbad, bad, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-  CK(cudaStreamSynchronize(h->st));
-  if (nbad) {
-    set_error("rho input has non-positive or non-finite values");
-    return CELL_EINVAL;
-  }
-  // vectors and Krylov scalars
-  const i64 len = 4 * nn;
+  h->kd.rho = h->rho64;
   CKS(A.alloc(&h->b64, 9 * len));
   CKS(A.alloc(&h->x64, 9 * len));
   CKS(A.alloc(&h->r64, 9 * len));
+  CKS(A.alloc(&h->xh, 9 * len));
+  CKS(A.alloc(&h->xl, 9 * len));
   h->nblk = (int)std::min<i64>(1024, std::max<i64>(1, (len + 4095) / 4096));
   CKS(A.alloc(&h->partial, (size_t)9 * 4 * h->nblk * kNvMax));
   CKS(A.alloc(&h->red, 9 * kNvMax));
@@ -679,23 +753,9 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(A.alloc(&h->want, 9));
   CKS(A.alloc(&h->ranmask, 9));
   CK(cudaMemsetAsync(h->x64, 0, 9 * len * sizeof(double), h->st));
-  {
-    double srho2 = 0.0;
-    cell::sum_reduce(h->rho64, nn, h->partial, h->nblk, h->red, h->st, 1);
-    CK(cudaMemcpyAsync(&srho2, h->red, sizeof(double), cudaMemcpyDeviceToHost, h->st));
-    CK(cudaStreamSynchronize(h->st));
-    for (int I = 0; I < 9; ++I) {
-      double f2 = 0.0;
-      for (int a = 0; a < 32; ++a) f2 += h->F[a * 9 + I] * h->F[a * 9 + I];
-      h->bfloor[I] = 1e-13 * std::sqrt(srho2 * f2);
-    }
-  }
-  // the FP64 operator serves the refinement residual in every precision mode
-  std::memcpy(h->kd.K0.k, h->K0, sizeof(h->kd.K0.k));
-  std::memcpy(h->kd.S0.k, h->S0, sizeof(h->kd.S0.k));
-  h->kd.rho = h->rho64;
   if (d->opt.precision == CELL_MIXED_FP32) CKS(setup_krylov<float>(h));
   else CKS(setup_krylov<double>(h));
+  CKS(load_design(h, d->input));
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   return CELL_OK;
@@ -713,6 +773,8 @@ int solve_impl(cell_handle* h, cell_stats* st) {
   std::memcpy(RP.F, h->F, sizeof(RP.F));
   cell::rhs9(h->rho64, RP, o.load_mask, h->b64, h->nx, h->ny, h->nz, s);
   CK(cudaMemsetAsync(h->x64, 0, 9 * len * sizeof(double), s));
+  CK(cudaMemsetAsync(h->xh, 0, 9 * len * sizeof(float), s));
+  CK(cudaMemsetAsync(h->xl, 0, 9 * len * sizeof(float), s));
   double bn2[9], rn2[9];
   cell::multidot<double>(h->b64, 0, len, 1, h->b64, len, len, h->partial, nblk, kNvMax, 9, nullptr, s);
   cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->red, 0, 9, nullptr, s);
@@ -750,9 +812,16 @@ int solve_impl(cell_handle* h, cell_stats* st) {
     CK(cudaMemcpyAsync(h->want, want, sizeof(want), cudaMemcpyHostToDevice, s));
     CKS(gmres_cycle<T>(h, tolabs, S.iters));
     ++refine;
-    // FP64 residual of the updated iterate: r = bhat - Ahat x
+    // FP64-grade residual of the updated iterate: r = bhat - Ahat x
     h->prof.cur_units = 9;
-    apply_full_T<double>(h, h->x64, len, h->r64, len, h->b64, len, -1.0, 1.0, nullptr, 9);
+    if constexpr (sizeof(T) == 4) {
+      const int ip = h->prof.begin(s);
+      cell::resid_df(h->xh, h->xl, len, h->b64, len, h->r64, len, h->rho32, h->rho_l, h->DF,
+                     h->nx, h->ny, h->nz, 9, nullptr, s);
+      h->prof.end(CELL_PROF_FULL64, ip, s);
+    } else {
+      apply_full_T<double>(h, h->x64, len, h->r64, len, h->b64, len, -1.0, 1.0, nullptr, 9);
+    }
   }
   // null-space projection (mean displacement and potential per load)
   cell::comp_sums(h->x64, h->nn, 9, h->partial, nblk, h->red2, s);
@@ -823,6 +892,11 @@ int cell_setup(const cell_desc* d, cell_handle** out) {
   }
   *out = h;
   return CELL_OK;
+}
+
+int cell_update(cell_handle* h, const void* input) {
+  if (!h || !input) return CELL_EINVAL;
+  return load_design(h, input);
 }
 
 int cell_solve(cell_handle* h, cell_stats* st) {
@@ -962,6 +1036,11 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype) {
     cell::FixedMat<double, 4> M;
     std::memcpy(M.k, h->K0, sizeof(M.k));
     cell::apply_full<double>(a, M, cell::AM_LINEAR, nrhs, h->st);
+  } else if (dtype == CELL_F64_DF) {
+    if (nrhs > 9) return CELL_EINVAL;
+    cell::split_f64(static_cast<const double*>(x), h->xh, h->xl, (i64)nrhs * len, h->st);
+    cell::resid_df(h->xh, h->xl, len, nullptr, 0, static_cast<double*>(y), len, h->rho32, h->rho_l,
+                   h->DF, h->nx, h->ny, h->nz, nrhs, nullptr, h->st);
   } else {
     return CELL_EINVAL;
   }

@@ -59,6 +59,7 @@ struct ApplyArgs {
   const T* dinv;           // [NC][nn] inverse diagonal
   const T* rho;            // per-element scale (fixed-matrix operators)
   const T* ke;             // per-element matrices, SoA: ke[entry*ne + e]
+  const T* st;             // assembled 27-point block stencil, SoA: st[((q*NC+c)*NC+d)*nn + n]
   T alpha, beta, c1, c2;
   int nx, ny, nz;
   int sol_zero;            // CHEB modes: incoming sol is implicitly zero
@@ -81,6 +82,29 @@ template <typename T> void apply_ss(const ApplyArgs<T>& a, const FixedMat<T, 1>&
 // Per-element-matrix operator on a coarse level (NC = 1 or 3).
 template <typename T, int NC> void apply_elem(const ApplyArgs<T>& a, int mode, int nrhs,
                                               cudaStream_t s);
+// Assembled-stencil operator on a coarse level (NC = 1 or 3), a.st set.
+template <typename T, int NC> void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs,
+                                                 cudaStream_t s);
+// Assemble the 27-point block stencil of a level from its element matrices.
+template <typename T, int NC> void stencil_from_elem(const T* ke, T* st, int nx, int ny, int nz,
+                                                     cudaStream_t s);
+
+// FP64-grade residual r = b - Ahat x (r = Ahat x if b is null) in FP32 double-float arithmetic: x is
+// given as FP32 pairs (x = xh + xl), K0 and rho likewise; products are
+// error-free (FMA), sums use TwoSum.  KH/KL: high/low FP32 parts of K0.
+struct DFMat {
+  float kh[1024];
+  float kl[1024];
+};
+void resid_df(const float* xh, const float* xl, i64 xs, const double* b, i64 bs, double* r, i64 rs,
+              const float* rho_h, const float* rho_l, const DFMat& M, int nx, int ny, int nz,
+              int nrhs, const int* active, cudaStream_t s);
+// xh = fp32(x), xl = fp32(x - xh) for n values
+void split_f64(const double* x, float* xh, float* xl, i64 n, cudaStream_t s);
+// x64 += sc[q] * d; xh = fp32(x64), xl = fp32(x64 - xh)
+template <typename T> void axpy_split(double* x, float* xh, float* xl, i64 xs, const T* d, i64 ds,
+                                      i64 len, const double* sc, int nrhs, const int* active,
+                                      cudaStream_t s);
 
 // ---- multigrid helpers (mg.cu) ----------------------------------------------
 template <typename T, int NC> void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds,
