@@ -62,6 +62,14 @@ def parse():
     return ap.parse_args()
 
 
+def traffic_table():
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return {}
+    with open(p) as f:
+        return {k: v for k, v in json.load(f).items() if not k.startswith("_") and v}
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -279,6 +287,10 @@ def main():
         peak = fp32_peak if kdt == "f32" else fp64_peak
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None}
+    tt = traffic_table().get(dom)
+    if tt and tt.get("n") == n and tt.get("bytes"):
+        roof["traffic"] = tt["bytes"] * per_launch_units / tt["loads"]
+        roof["traffic_source"] = "profiles/kernels_64cube.md (ncu dram__bytes_read+write, 9-load launch, scaled)"
     roof.update({"kernel": dom, "peak_source": f"{'hbm ' + hbm_kind if bound == 'hbm' else 'unit counts x max SM clock'}",
                  "launches": cnt[dom], "avg_launch_ms": avg_ms,
                  "dof_rhs_per_s": 4 * nn * per_launch_units / (avg_ms * 1e-3),

@@ -71,7 +71,8 @@ typedef enum cell_input_kind {
 typedef enum cell_dtype {
   CELL_F32 = 0,
   CELL_F64 = 1,
-  CELL_F64_DF = 2   /* FP64 data, arithmetic in FP32 pairs (cell_apply only) */
+  CELL_F64_DF = 2,  /* FP64 data, arithmetic in FP32 pairs (cell_apply only) */
+  CELL_F32_TC = 3   /* FP32 data, TF32 tensor-core element contraction (cell_apply only) */
 } cell_dtype;
 
 typedef struct cell_options {
@@ -94,6 +95,13 @@ typedef struct cell_options {
   int coarse_dofs;     /* stop coarsening once a level has at most this many dofs */
   int load_mask;       /* bit I set = solve load I (default 0x1FF = all nine) */
   int profile;         /* nonzero: time kernel classes with CUDA events (cell_stats) */
+  int tensor_cores;    /* MIXED: 0 = SIMT FP32 applies only (default); 1 = fine-grid elastic
+                          smoothing applies on tcgen05 tensor cores (TF32 element
+                          contraction, FP32 accumulate); 2 = also the Krylov operator.
+                          Used where nx % 16 == 0, ny % 4 == 0, nz % 2 == 0. */
+  int const_bank;      /* MIXED: nonzero (default) = FP32 element matrices in one of 4
+                          library-wide __constant__ slots (shared by handles with equal
+                          matrices), falling back to kernel parameters if all are taken */
 } cell_options;
 
 typedef struct cell_desc {
@@ -200,7 +208,10 @@ int cell_get_solution(cell_handle* h, double* out);
  * CELL_F64_DF: FP64 vectors (nrhs <= 9), evaluated with the FP32 double-float
  * kernel that the mixed solver uses for its FP64-grade residuals (error-free
  * FMA products, TwoSum accumulation); it overwrites the handle's internal
- * split-iterate buffers, so call it only between solves. */
+ * split-iterate buffers, so call it only between solves.
+ * CELL_F32_TC: FP32 vectors through the tcgen05 tensor-core kernel (TF32
+ * inputs, FP32 accumulation); CELL_EINVAL if the grid does not tile into
+ * 16 x 4 x 2 node bricks. */
 int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype);
 
 /* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as

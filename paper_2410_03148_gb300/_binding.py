@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libcell.so")
 CELL_OK, CELL_EINVAL, CELL_ENOMEM, CELL_ENOTCONV, CELL_ETIMEOUT, CELL_ECUDA, CELL_ESTATE = range(7)
 CELL_FP64, CELL_MIXED_FP32 = 0, 1
 CELL_INPUT_RHO, CELL_INPUT_PHI = 0, 1
-CELL_F32, CELL_F64, CELL_F64_DF = 0, 1, 2
+CELL_F32, CELL_F64, CELL_F64_DF, CELL_F32_TC = 0, 1, 2, 3
 
 # every symbol include/cell.h declares
 EXPORTS = [
@@ -36,7 +36,8 @@ class cell_options(C.Structure):
         ("inner_tol", C.c_double), ("max_refine", C.c_int), ("vcycles_u", C.c_int),
         ("vcycles_phi", C.c_int), ("cheb_degree", C.c_int), ("cheb_lo", C.c_double),
         ("cheb_hi", C.c_double), ("schur_shift", C.c_double), ("coarse_dofs", C.c_int),
-        ("load_mask", C.c_int), ("profile", C.c_int),
+        ("load_mask", C.c_int), ("profile", C.c_int), ("tensor_cores", C.c_int),
+        ("const_bank", C.c_int),
     ]
 
 

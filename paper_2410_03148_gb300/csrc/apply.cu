@@ -12,6 +12,9 @@
 //
 // Operator definitions: Eq. (sym-piezo) and its nonsymmetric second form
 // (potential rows negated), §2.5; block operators of P_SCP, §2.5.3.
+#include <cstring>
+#include <mutex>
+
 #include "kernels.cuh"
 
 namespace cell {
@@ -74,13 +77,34 @@ __device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const Nod
   }
 }
 
+// Constant-bank slots for the FP32 element matrices: a kernel instantiated
+// for a slot reads its coefficients at compile-time offsets of a __constant__
+// array, which the compiler can fold into the FMA instructions as operands.
+// Slots are shared by handles with equal matrices (reference counted, per
+// device); kernel parameters remain the fallback when all slots are taken.
+constexpr int kSlots = 4;
+__constant__ float c_k0[kSlots][1024];
+__constant__ float c_s0[kSlots][64];
+
+template <typename T, int NCM>
+struct ParamCoef {
+  const FixedMat<T, NCM>& M;
+  __device__ __forceinline__ T operator()(int i) const { return M.k[i]; }
+};
+template <int SLOT, int NCM>
+struct ConstCoef {
+  __device__ __forceinline__ float operator()(int i) const {
+    if constexpr (NCM == 4) return c_k0[SLOT][i];
+    else return c_s0[SLOT][i];
+  }
+};
+
 // Fixed-matrix operator, FP32: the 27 neighbours are preloaded into registers
 // and every coefficient index is a compile-time constant.  Neighbour offsets
 // are 32-bit and each component plane has its own base pointer, so a load is
 // one address multiply-add.
-template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
-__global__ void __launch_bounds__(kBlock)
-k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
+template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE, typename COEF>
+__device__ __forceinline__ void apply_fixed_pre_body(const ApplyArgs<T>& a, const COEF& Kc) {
   const int r = blockIdx.z;
   if (a.active && !a.active[r]) return;
   const int nx = a.nx, ny = a.ny;
@@ -124,7 +148,7 @@ k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM>
       for (int c = 0; c < NCO; ++c)
 #pragma unroll
         for (int d = 0; d < NCI; ++d)
-          tl[c] = fma(M.k[(la * NCM + R0 + c) * (8 * NCM) + b * NCM + C0 + d], xs[q][d], tl[c]);
+          tl[c] = fma(Kc((la * NCM + R0 + c) * (8 * NCM) + b * NCM + C0 + d), xs[q][d], tl[c]);
     }
 #pragma unroll
     for (int c = 0; c < NCO; ++c) acc[c] = fma(w, tl[c], acc[c]);
@@ -134,6 +158,17 @@ k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM>
 #pragma unroll
   for (int c = 0; c < NCO; ++c) dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? xs[13][c] : T(0);
   epilogue<T, NCO, MODE>(a, r, t, acc, dold);
+}
+
+template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
+__global__ void __launch_bounds__(kBlock)
+k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
+  apply_fixed_pre_body<T, NCM, NCI, NCO, R0, C0, NEGLAST, MODE>(a, ParamCoef<T, NCM>{M});
+}
+
+template <int SLOT, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
+__global__ void __launch_bounds__(kBlock) k_apply_fixed_cslot(const ApplyArgs<float> a) {
+  apply_fixed_pre_body<float, NCM, NCI, NCO, R0, C0, NEGLAST, MODE>(a, ConstCoef<SLOT, NCM>{});
 }
 
 // Fixed-matrix operator, FP64: neighbours are loaded per element (FP64
@@ -341,57 +376,51 @@ __device__ __forceinline__ void two_sum(float& s, float& lo, float p) {
   s = t;
 }
 
-// r = b - Ahat x with FP64-grade accuracy from FP32 arithmetic only.
+// r = b - Ahat x with FP64-grade accuracy from FP32 arithmetic only.  One
+// thread per (node, output component, load): the compensated sum of each
+// row is one TwoSum chain, registers stay low and occupancy high.
 __global__ void __launch_bounds__(kBlock)
 k_resid_df(const float* __restrict__ xh, const float* __restrict__ xl, i64 xs,
            const double* __restrict__ b, i64 bs, double* __restrict__ r, i64 rs,
            const float* __restrict__ rho_h, const float* __restrict__ rho_l,
            const __grid_constant__ DFMat M, int nx, int ny, int nz, const int* active) {
-  const int q = blockIdx.z;
+  const int q = blockIdx.z >> 2, c = blockIdx.z & 3;
   if (active && !active[q]) return;
   NodeIdx t;
   if (!node_index(nx, ny, nz, t)) return;
   const float* XH = xh + q * xs;
   const float* XL = xl + q * xs;
-  float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+  float ah = 0.f, al = 0.f;
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
     const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
     const i64 el = t.xo[ex] + t.yo[ey] + t.zo[ez];
-    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+    float sh = 0.f, sl = 0.f;
 #pragma unroll
     for (int bn = 0; bn < 8; ++bn) {
       const i64 m = t.xo[ex + (bn & 1)] + t.yo[ey + ((bn >> 1) & 1)] + t.zo[ez + (bn >> 2)];
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
         const float vh = __ldg(XH + d * t.nn + m), vl = __ldg(XL + d * t.nn + m);
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int k = (la * 4 + c) * 32 + bn * 4 + d;
-          const float p = M.kh[k] * vh;
-          const float pe = fmaf(M.kh[k], vh, -p);
-          two_sum(sh[c], sl[c], p);
-          sl[c] = fmaf(M.kh[k], vl, fmaf(M.kl[k], vh, sl[c] + pe));
-        }
+        const int k = (la * 4 + c) * 32 + bn * 4 + d;
+        const float kh = M.kh[k], kl = M.kl[k];
+        const float p = kh * vh;
+        const float pe = fmaf(kh, vh, -p);
+        two_sum(sh, sl, p);
+        sl = fmaf(kh, vl, fmaf(kl, vh, sl + pe));
       }
     }
     const float wh = __ldg(rho_h + el), wl = __ldg(rho_l + el);
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const float p = sh[c] * wh;
-      const float pe = fmaf(sh[c], wh, -p);
-      two_sum(ah[c], al[c], p);
-      al[c] = fmaf(sh[c], wl, fmaf(sl[c], wh, al[c] + pe));
-    }
+    const float p = sh * wh;
+    const float pe = fmaf(sh, wh, -p);
+    two_sum(ah, al, p);
+    al = fmaf(sh, wl, fmaf(sl, wh, al + pe));
   }
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    double v = (double)ah[c] + (double)al[c];
-    if (c == 3) v = -v;
-    const i64 o = (i64)c * t.nn + t.n;
-    r[q * rs + o] = b ? b[q * bs + o] - v : v;
-  }
+  double v = (double)ah + (double)al;
+  if (c == 3) v = -v;
+  const i64 o = (i64)c * t.nn + t.n;
+  r[q * rs + o] = b ? b[q * bs + o] - v : v;
 }
 
 __global__ void k_axpy_split_f(double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
@@ -430,11 +459,23 @@ inline dim3 grid_for(const ApplyArgs<T>& a, int nrhs) {
   return dim3((unsigned)((plane + kBlock - 1) / kBlock), (unsigned)a.nz, (unsigned)nrhs);
 }
 
+template <int NCM, int NCI, int NCO, int R0, int C0, bool NEG, int MODE>
+void launch_cslot(const ApplyArgs<float>& a, int nrhs, cudaStream_t s) {
+  const dim3 g = grid_for(a, nrhs);
+  switch (a.cslot1 - 1) {
+    case 0: note_launch(), k_apply_fixed_cslot<0, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+    case 1: note_launch(), k_apply_fixed_cslot<1, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+    case 2: note_launch(), k_apply_fixed_cslot<2, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+    default: note_launch(), k_apply_fixed_cslot<3, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+  }
+}
+
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEG, int MODE>
 void launch_fixed(const ApplyArgs<T>& a, const FixedMat<T, NCM>& M, int nrhs, cudaStream_t s) {
-  if constexpr (sizeof(T) == 4)
-    note_launch(), k_apply_fixed_pre<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
-  else
+  if constexpr (sizeof(T) == 4) {
+    if (a.cslot1 > 0) launch_cslot<NCM, NCI, NCO, R0, C0, NEG, MODE>(a, nrhs, s);
+    else note_launch(), k_apply_fixed_pre<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
+  } else
     note_launch(), k_apply_fixed_ld<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
 }
 
@@ -525,8 +566,8 @@ void resid_df(const float* xh, const float* xl, i64 xs, const double* b, i64 bs,
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
-  note_launch(), k_resid_df<<<grid_for(a, nrhs), kBlock, 0, s>>>(xh, xl, xs, b, bs, r, rs, rho_h, rho_l, M,
-                                                                  nx, ny, nz, active);
+  note_launch(), k_resid_df<<<grid_for(a, 4 * nrhs), kBlock, 0, s>>>(xh, xl, xs, b, bs, r, rs, rho_h, rho_l, M,
+                                                                      nx, ny, nz, active);
 }
 
 __global__ void k_split(const double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
@@ -559,6 +600,52 @@ template void axpy_split<float>(double*, float*, float*, i64, const float*, i64,
                                 int, const int*, cudaStream_t);
 template void axpy_split<double>(double*, float*, float*, i64, const double*, i64, i64,
                                  const double*, int, const int*, cudaStream_t);
+
+// ---- constant-bank slot manager ---------------------------------------------
+namespace {
+struct SlotState {
+  int refs = 0;
+  float k0[1024];
+  float s0[64];
+};
+std::mutex g_slot_mu;
+SlotState g_slots[64][kSlots];
+}  // namespace
+
+int cslot_acquire(const float* K0f, const float* S0f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  for (int i = 0; i < kSlots; ++i) {
+    SlotState& st = g_slots[dev][i];
+    if (st.refs > 0 && !std::memcmp(st.k0, K0f, sizeof(st.k0)) && !std::memcmp(st.s0, S0f, sizeof(st.s0))) {
+      ++st.refs;
+      return i + 1;
+    }
+  }
+  for (int i = 0; i < kSlots; ++i) {
+    SlotState& st = g_slots[dev][i];
+    if (st.refs == 0) {
+      if (cudaMemcpyToSymbol(c_k0, K0f, 1024 * sizeof(float), (size_t)i * 1024 * sizeof(float)) != cudaSuccess ||
+          cudaMemcpyToSymbol(c_s0, S0f, 64 * sizeof(float), (size_t)i * 64 * sizeof(float)) != cudaSuccess)
+        return 0;
+      std::memcpy(st.k0, K0f, sizeof(st.k0));
+      std::memcpy(st.s0, S0f, sizeof(st.s0));
+      st.refs = 1;
+      return i + 1;
+    }
+  }
+  return 0;
+}
+
+void cslot_release(int slot1) {
+  if (slot1 <= 0) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  SlotState& st = g_slots[dev][slot1 - 1];
+  if (st.refs > 0) --st.refs;
+}
 
 #define INST(T)                                                                                   \
   template void apply_full<T>(const ApplyArgs<T>&, const FixedMat<T, 4>&, int, int, cudaStream_t); \

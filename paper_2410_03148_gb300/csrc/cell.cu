@@ -183,6 +183,10 @@ struct cell_handle {
   // mixed path: x64 as FP32 pairs and rho's low part, for the double-float residual
   float *xh = nullptr, *xl = nullptr, *rho_l = nullptr, *rho_tmp = nullptr;
   int* bad = nullptr;
+  int* tc_err = nullptr;   // tensor-core kernels: expired bounded waits
+  bool tc_ok = false;      // grid tiles into tensor-core bricks
+  cell::TcTables tct;      // tensor-core operand tables (device)
+  int cslot1 = 0;          // constant-bank slot of the FP32 element matrices (+1)
   cell::DFMat DF;
   double *partial = nullptr, *red = nullptr, *red2 = nullptr;
   int nblk = 0;
@@ -193,7 +197,7 @@ struct cell_handle {
   double *H = nullptr, *cs = nullptr, *sn = nullptr, *g = nullptr, *hcol = nullptr, *hnorm = nullptr;
   double *resid = nullptr, *invscale = nullptr, *tolabs = nullptr, *ybuf = nullptr, *beta2 = nullptr;
   double* ones = nullptr;
-  int *active = nullptr, *kcount = nullptr, *want = nullptr, *ranmask = nullptr;
+  int *active = nullptr, *kcount = nullptr, *want = nullptr, *ranmask = nullptr, *reorth = nullptr;
   Krylov<float> kf;
   Krylov<double> kd;
   bool solved = false;
@@ -225,12 +229,19 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
   a.nz = L.nz;
   a.dinv = L.dinv;
   a.active = mask;
+  a.cslot1 = h->cslot1;
   Krylov<T>& K = kry<T>(h);
   const int ip = h->prof.begin(h->st);
   if (l == 0) {
     a.rho = K.rho;
-    if (NC == 3) cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
-    else cell::apply_ss<T>(a, K.S0, mode, 9, h->st);
+    if constexpr (sizeof(T) == 4 && NC == 3) {
+      if (h->tc_ok && h->d.opt.tensor_cores >= 1) cell::apply_tc_uu(a, h->tct, mode, 9, h->tc_err, h->st);
+      else cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
+    } else if constexpr (NC == 3) {
+      cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
+    } else {
+      cell::apply_ss<T>(a, K.S0, mode, 9, h->st);
+    }
   } else {
     a.st = L.st;
     cell::apply_stencil<T, NC>(a, mode, 9, h->st);
@@ -483,6 +494,7 @@ void precond(cell_handle* h, const T* v, T* z, const int* mask) {
   a.x = z; a.xs = len; a.y = K.tphi; a.ys = nn; a.b = v + 3 * nn; a.bs = len;
   a.alpha = T(1); a.beta = T(1); a.rho = K.rho; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
   a.active = mask;
+  a.cslot1 = h->cslot1;
   const int ip = h->prof.begin(h->st);
   cell::apply_pu<T>(a, K.K0, 9, h->st);
   h->prof.end(CELL_PROF_COUPLING, ip, h->st);
@@ -495,9 +507,14 @@ void apply_full_T(cell_handle* h, const T* x, i64 xs, T* y, i64 ys, const T* b, 
   cell::ApplyArgs<T> a{};
   a.x = x; a.xs = xs; a.y = y; a.ys = ys; a.b = b; a.bs = bs; a.alpha = alpha; a.beta = beta;
   a.rho = rho_of<T>(h); a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.active = mask;
+  a.cslot1 = h->cslot1;
   const int ip = h->prof.begin(h->st);
-  if constexpr (sizeof(T) == 4) cell::apply_full<T>(a, h->kf.K0, cell::AM_LINEAR, nrhs, h->st);
-  else cell::apply_full<T>(a, h->kd.K0, cell::AM_LINEAR, nrhs, h->st);
+  if constexpr (sizeof(T) == 4) {
+    if (h->tc_ok && h->d.opt.tensor_cores >= 2) cell::apply_tc_full(a, h->tct, nrhs, h->tc_err, h->st);
+    else cell::apply_full<T>(a, h->kf.K0, cell::AM_LINEAR, nrhs, h->st);
+  } else {
+    cell::apply_full<T>(a, h->kd.K0, cell::AM_LINEAR, nrhs, h->st);
+  }
   h->prof.end(sizeof(T) == 4 ? CELL_PROF_FULL32 : CELL_PROF_FULL64, ip, h->st);
 }
 
@@ -576,16 +593,22 @@ int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
     T* w = K.V + (i64)(j + 1) * vstride;
     precond<T>(h, vj, K.z, h->active);
     apply_full_T<T>(h, K.z, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
-    // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2 (with |w|^2)
+    // Classical Gram-Schmidt with selective reorthogonalisation: one pass of
+    // dots (w is V_{j+1}, so the same pass also gives |w|^2), one update with
+    // the new norm, and a second pass only for loads whose norm dropped below
+    // 1/sqrt(2) of its value before the pass.
     const int ipk = h->prof.begin(s);
-    cell::multidot<T>(K.V, vstride, len, j + 1, w, len, len, h->partial, nblk, kNvMax, 9, h->active, s);
-    cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->hcol, 0, 9, h->active, s);
-    cell::update<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, 1, h->partial, nblk, 9, h->active, s);
-    cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->ybuf, 0, 9, h->active, s);
-    cell::update<T>(K.V, vstride, len, j + 1, h->ybuf, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->active, s);
+    cell::multidot<T>(K.V, vstride, len, j + 2, w, len, len, h->partial, nblk, kNvMax, 9, h->active, s);
+    cell::reduce_partials(h->partial, nblk, j + 2, kNvMax, h->hcol, 0, 9, h->active, s);
+    cell::update<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->active, s);
     cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->active, s);
+    cell::reorth_flag(h->hcol, h->hnorm, j, h->active, h->reorth, 9, s);
+    cell::multidot<T>(K.V, vstride, len, j + 1, w, len, len, h->partial, nblk, kNvMax, 9, h->reorth, s);
+    cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->ybuf, 0, 9, h->reorth, s);
+    cell::update<T>(K.V, vstride, len, j + 1, h->ybuf, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->reorth, s);
+    cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->reorth, s);
     // hcol += second-pass coefficients (a one-block "reduction" of ybuf)
-    cell::reduce_partials(h->ybuf, 1, j + 1, kNvMax, h->hcol, 1, 9, h->active, s);
+    cell::reduce_partials(h->ybuf, 1, j + 1, kNvMax, h->hcol, 1, 9, h->reorth, s);
     h->prof.end(CELL_PROF_KRYLOV, ipk, s);
     cell::givens_step(h->H, h->cs, h->sn, h->g, h->hcol, h->hnorm, j, m, h->active, h->resid,
                       h->tolabs, h->invscale, h->kcount, 9, s);
@@ -626,6 +649,7 @@ int check_options(const cell_options& o) {
   if (!(o.cheb_lo > 0.0 && o.cheb_lo < 1.0) || !(o.cheb_hi > 0.0)) return CELL_EINVAL;
   if (!(o.schur_shift >= 0.0) || o.coarse_dofs < 1) return CELL_EINVAL;
   if ((o.load_mask & 0x1FF) == 0 || (o.load_mask & ~0x1FF)) return CELL_EINVAL;
+  if (o.tensor_cores < 0 || o.tensor_cores > 2) return CELL_EINVAL;
   return CELL_OK;
 }
 
@@ -719,6 +743,29 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(A.alloc(&h->rho_l, nn));
   CKS(A.alloc(&h->rho_tmp, nn));
   CKS(A.alloc(&h->bad, 1));
+  CKS(A.alloc(&h->tc_err, 1));
+  CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st));
+  h->tc_ok = cell::tc_shape_ok(h->nx, h->ny, h->nz);
+  if (h->tc_ok) {
+    std::vector<float> bu(cell::tc_table_floats(3)), bf(cell::tc_table_floats(4));
+    std::vector<unsigned short> gu(cell::tc_table_idx(3)), gf(cell::tc_table_idx(4));
+    cell::tc_build_tables_host(h->K0, bu.data(), gu.data(), bf.data(), gf.data());
+    float *dbu, *dbf;
+    unsigned short *dgu, *dgf;
+    CKS(A.alloc(&dbu, bu.size()));
+    CKS(A.alloc(&dbf, bf.size()));
+    CKS(A.alloc(&dgu, gu.size()));
+    CKS(A.alloc(&dgf, gf.size()));
+    CK(cudaMemcpy(dbu, bu.data(), bu.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dbf, bf.data(), bf.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dgu, gu.data(), gu.size() * 2, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(dgf, gf.data(), gf.size() * 2, cudaMemcpyHostToDevice));
+    h->tct.b_uu = dbu;
+    h->tct.b_full = dbf;
+    h->tct.g_uu = dgu;
+    h->tct.g_full = dgf;
+  }
+  for (int i = 0; i < 1024; ++i) h->kf.K0.k[i] = (float)h->K0[i];
   CKS(A.alloc(&h->K0dev, 1024));
   CK(cudaMemcpyAsync(h->K0dev, h->K0, 1024 * sizeof(double), cudaMemcpyHostToDevice, h->st));
   h->kd.rho = h->rho64;
@@ -752,9 +799,17 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(A.alloc(&h->kcount, 9));
   CKS(A.alloc(&h->want, 9));
   CKS(A.alloc(&h->ranmask, 9));
+  CKS(A.alloc(&h->reorth, 9));
   CK(cudaMemsetAsync(h->x64, 0, 9 * len * sizeof(double), h->st));
-  if (d->opt.precision == CELL_MIXED_FP32) CKS(setup_krylov<float>(h));
-  else CKS(setup_krylov<double>(h));
+  if (d->opt.precision == CELL_MIXED_FP32) {
+    float k0f[1024], s0f[64];
+    for (int i = 0; i < 1024; ++i) k0f[i] = (float)h->K0[i];
+    for (int i = 0; i < 64; ++i) s0f[i] = (float)h->S0[i];
+    if (d->opt.const_bank) h->cslot1 = cell::cslot_acquire(k0f, s0f);
+    CKS(setup_krylov<float>(h));
+  } else {
+    CKS(setup_krylov<double>(h));
+  }
   CKS(load_design(h, d->input));
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
@@ -826,7 +881,14 @@ int solve_impl(cell_handle* h, cell_stats* st) {
   // null-space projection (mean displacement and potential per load)
   cell::comp_sums(h->x64, h->nn, 9, h->partial, nblk, h->red2, s);
   cell::sub_means(h->x64, h->nn, 9, h->red2, s);
+  int tcerr = 0;
+  CK(cudaMemcpyAsync(&tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
+  if (tcerr) {
+    set_error("a tensor-core kernel's bounded wait expired");
+    status = CELL_ETIMEOUT;
+    CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+  }
   CK(cudaGetLastError());
   auto t1 = std::chrono::steady_clock::now();
   S.solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
@@ -867,6 +929,8 @@ void cell_default_options(cell_options* o) {
   o->coarse_dofs = 200;
   o->load_mask = 0x1FF;
   o->profile = 0;
+  o->tensor_cores = 0;
+  o->const_bank = 1;
 }
 
 int cell_setup(const cell_desc* d, cell_handle** out) {
@@ -1036,6 +1100,12 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype) {
     cell::FixedMat<double, 4> M;
     std::memcpy(M.k, h->K0, sizeof(M.k));
     cell::apply_full<double>(a, M, cell::AM_LINEAR, nrhs, h->st);
+  } else if (dtype == CELL_F32_TC) {
+    if (!h->tc_ok) return CELL_EINVAL;
+    cell::ApplyArgs<float> a{};
+    a.x = static_cast<const float*>(x); a.xs = len; a.y = static_cast<float*>(y); a.ys = len;
+    a.alpha = 1.f; a.rho = h->rho32; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    cell::apply_tc_full(a, h->tct, nrhs, h->tc_err, h->st);
   } else if (dtype == CELL_F64_DF) {
     if (nrhs > 9) return CELL_EINVAL;
     cell::split_f64(static_cast<const double*>(x), h->xh, h->xl, (i64)nrhs * len, h->st);
@@ -1076,6 +1146,7 @@ int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]) {
 void cell_destroy(cell_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  cell::cslot_release(h->cslot1);
   h->arena.release();
   delete h;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <cstddef>
 #include <cstdint>
 
 namespace cell {
@@ -64,7 +65,13 @@ struct ApplyArgs {
   int nx, ny, nz;
   int sol_zero;            // CHEB modes: incoming sol is implicitly zero
   const int* active;       // per-rhs flag (nullptr = all active)
+  int cslot1;              // FP32 fixed-matrix kernels: constant-bank slot + 1 (0 = use parameter)
 };
+
+// Constant-bank slots holding (K0, S0) in FP32 for the fixed-matrix kernels;
+// returns slot + 1, or 0 if none is free.  Release with cslot_release.
+int cslot_acquire(const float* K0f, const float* S0f);
+void cslot_release(int slot1);
 
 // ---- operator applies (apply.cu) -------------------------------------------
 // Full nonsymmetric operator Ahat (4 -> 4 comps, potential rows negated).
@@ -105,6 +112,25 @@ void split_f64(const double* x, float* xh, float* xl, i64 n, cudaStream_t s);
 template <typename T> void axpy_split(double* x, float* xh, float* xl, i64 xs, const T* d, i64 ds,
                                       i64 len, const double* sc, int nrhs, const int* active,
                                       cudaStream_t s);
+
+// Tensor-core (tcgen05, 3xTF32) element applies (apply_tc.cu); the grid must
+// satisfy tc_shape_ok.  err counts bounded-wait expiries.  The tables (element
+// block in the operand layout, hi and lo TF32 parts; gather indices) are built
+// on the host once per material and grid.
+struct TcTables {
+  const float* b_uu = nullptr;
+  const unsigned short* g_uu = nullptr;
+  const float* b_full = nullptr;
+  const unsigned short* g_full = nullptr;
+};
+bool tc_shape_ok(int nx, int ny, int nz);
+size_t tc_table_floats(int nc);
+size_t tc_table_idx(int nc);
+void tc_build_tables_host(const double* K0, float* b_uu, unsigned short* g_uu, float* b_full,
+                          unsigned short* g_full);
+void apply_tc_uu(const ApplyArgs<float>& a, const TcTables& T, int mode, int nrhs, int* err,
+                 cudaStream_t s);
+void apply_tc_full(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cudaStream_t s);
 
 // ---- multigrid helpers (mg.cu) ----------------------------------------------
 template <typename T, int NC> void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds,
@@ -150,6 +176,9 @@ void givens_step(double* H, double* cs, double* sn, double* g, const double* hco
                  double* invscale, int* kcount, int nrhs, cudaStream_t s);
 void backsolve(const double* H, const double* g, const int* kcount, int m, double* y, int nrhs,
                const int* mask, cudaStream_t s);
+// reorth[q] = active[q] && |w_new|^2 < |w_old|^2 / 2 (|w_old|^2 in hcol[q][j+1])
+void reorth_flag(const double* hcol, const double* hnorm2, int j, const int* active, int* reorth,
+                 int nrhs, cudaStream_t s);
 void start_cycle(const double* beta2, double* g, int m, int* active, const int* want, double* resid,
                  double* invscale, const double* tolabs, int* kcount, int nrhs, cudaStream_t s);
 // v32[q] = (float)(r64[q] * sc[q])   or  x64[q] += sc[q] * d32[q]

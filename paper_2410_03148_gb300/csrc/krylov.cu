@@ -221,6 +221,17 @@ __global__ void k_givens(double* H, double* cs, double* sn, double* g, const dou
   if (res <= tolabs[q] || brk || j + 1 >= m) active[q] = 0;
 }
 
+// Reorthogonalisation test ("twice is enough"): after one classical
+// Gram-Schmidt pass, repeat it for load q only if the new norm fell below
+// 1/sqrt(2) of the norm before the pass (hcol[j+1] holds |w|^2 before).
+__global__ void k_reorth_flag(const double* hcol, const double* hnorm2, int j, int nvmax,
+                              const int* active, int* reorth, int nrhs) {
+  const int q = threadIdx.x;
+  if (q >= nrhs) return;
+  const double before = hcol[q * nvmax + j + 1];
+  reorth[q] = (active[q] && hnorm2[q * nvmax] < 0.5 * before) ? 1 : 0;
+}
+
 // Solve the k x k upper-triangular R y = g per rhs (mask: rhs that ran this cycle).
 __global__ void k_backsolve(const double* H, const double* g, const int* kcount, int m, double* y,
                             int nvmax, int nrhs, const int* mask) {
@@ -329,6 +340,11 @@ void givens_step(double* H, double* cs, double* sn, double* g, const double* hco
                  const double* tolabs, double* invscale, int* kcount, int nrhs, cudaStream_t s) {
   note_launch(), k_givens<<<1, 32, 0, s>>>(H, cs, sn, g, hcol, hnorm2, j, m, 64, active, resid, tolabs, invscale,
                             kcount, nrhs);
+}
+
+void reorth_flag(const double* hcol, const double* hnorm2, int j, const int* active, int* reorth,
+                 int nrhs, cudaStream_t s) {
+  note_launch(), k_reorth_flag<<<1, 32, 0, s>>>(hcol, hnorm2, j, 64, active, reorth, nrhs);
 }
 
 void backsolve(const double* H, const double* g, const int* kcount, int m, double* y, int nrhs,

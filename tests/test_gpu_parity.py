@@ -84,6 +84,48 @@ def test_apply_matches_oracle_matvec(shape, dtype):
     assert np.abs(y - yref).max() < tol * scale
 
 
+@pytest.mark.parametrize("shape", [(2, 4, 16), (4, 8, 32), (16, 16, 16), (6, 12, 48)])
+def test_tensor_core_apply_matches_oracle_matvec(shape):
+    """tcgen05 element contraction with the 3xTF32 split (x = xh + xl,
+    K = Kh + Kl, products xh Kh + xh Kl + xl Kh): FP32-level accuracy, like
+    the SIMT FP32 kernel."""
+    from paper_2410_03148_gb300 import _binding as B
+    rho = cellgen.random_rho(shape, seed=3)
+    cell = make_cell(rho, "rho")
+    P = fem.CellProblem(rho, *MAT)
+    rng = np.random.default_rng(6)
+    x = rng.standard_normal((3, 4) + shape)
+    xt = torch.as_tensor(x, device=dev(), dtype=torch.float32)
+    y = torch.empty_like(xt)
+    B.cell_apply(cell._h, xt.data_ptr(), y.data_ptr(), 3, B.CELL_F32_TC)
+    yref = from_dof(negate_phi_rows(P.Kg @ to_dof(x)), shape)
+    scale = np.abs(P.Kg).max() * np.abs(x).max() * 8
+    err = np.abs(y.double().cpu().numpy() - yref).max()
+    assert err < 2e-6 * scale, err / scale
+
+
+@pytest.mark.parametrize("tc", [0, 1, 2])
+@pytest.mark.parametrize("shape", [(16, 16, 16), (4, 8, 32)])
+def test_solve_with_tensor_cores_matches_oracle(shape, tc):
+    phi, ref = oracle_levelset(shape, 1)
+    cell = make_cell(phi, "phi", precision=1, tensor_cores=tc)
+    st = cell.solve()
+    assert max(st["rel_residual"]) <= 1e-10
+    errs = block_errors(*cell.homogenise(), ref)
+    assert max(errs) < 1e-8, (errs, st)
+
+
+@pytest.mark.parametrize("tc", [0, 1, 2])
+def test_laminate_with_tensor_cores_64(tc):
+    shape = (64, 64, 64)
+    rho = cellgen.laminate_rho(shape, 2, seed=21)
+    cell = make_cell(rho, "rho", precision=1, tensor_cores=tc)
+    cell.solve()
+    Cr, er, kr, _ = laminate.laminate_tensors(*MAT, rho[:, 0, 0], 2)
+    errs = block_errors(*cell.homogenise(), {"C": Cr, "e": er, "kappa": kr})
+    assert max(errs) < 1e-8, errs
+
+
 @pytest.mark.parametrize("shape", [(5, 6, 7), (32, 32, 32)])
 def test_double_float_apply_matches_fp64(shape):
     """The FP32 double-float operator (the mixed solver's FP64-grade residual)
@@ -236,6 +278,21 @@ def test_bitwise_reproducible():
         res.append(np.concatenate([a.ravel() for a in cell.homogenise()]))
         cell.close()
     assert np.array_equal(res[0], res[1])
+
+
+def test_constant_bank_and_parameter_kernels_agree():
+    """The element matrix read from a __constant__ slot or from the kernel
+    parameter gives the same solve (same arithmetic, possibly different
+    instruction order)."""
+    phi = cellgen.gaussian_levelset(16, seed=13)
+    out = []
+    for cb in (0, 1):
+        cell = make_cell(phi, "phi", const_bank=cb)
+        cell.solve()
+        out.append(cell.homogenise())
+        cell.close()
+    for a, b in zip(*out):
+        assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
 
 
 def test_update_equals_fresh_setup():
