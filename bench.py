@@ -219,7 +219,10 @@ def main():
     # One handle per process (all device memory allocated here, once); every
     # step maps a new design into it (cell_update: rho_e and the multigrid
     # hierarchy, S1) and runs S2-S9 on it, as an optimisation loop does.
-    cells = {p: Cell(designs[0], mat, kind="phi", precision=prec, profile=p) for p in (0, 1)}
+    # Handle 1 times every kernel class (class shares, untimed pass); handle 2
+    # times only the dominant class inside the timed region (its roofline).
+    cells = {0: Cell(designs[0], mat, kind="phi", precision=prec),
+             1: Cell(designs[0], mat, kind="phi", precision=prec, profile=1)}
 
     def step(phi, profile=0):
         cell = cells[profile]
@@ -237,6 +240,13 @@ def main():
 
     for w in range(args.warmup):
         step(designs[w % ndes])
+    # class shares from a fully profiled pass over the timed designs (untimed)
+    shares = [step(designs[k % ndes], profile=1)[0] for k in range(min(args.steps, 2))]
+    share_ms = {c: sum(s_["class_ms"][c] for s_ in shares) / len(shares) for c in B.PROF_CLASSES}
+    dom = max((c for c in CLASS_COST), key=lambda c: share_ms[c])
+    cells[2] = Cell(designs[0], mat, kind="phi", precision=prec, profile=1,
+                    profile_mask=1 << B.PROF_CLASSES.index(dom))
+    step(designs[0], profile=2)
     barrier()
     sampler = ClockSampler(local)
     sampler.start()
@@ -250,7 +260,7 @@ def main():
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        st, _, _ = step(designs[k % ndes], profile=1)
+        st, _, _ = step(designs[k % ndes], profile=2)
         e1.record(stream)
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
@@ -271,7 +281,6 @@ def main():
     tot = {c: sum(s["class_ms"][c] for s in stats) for c in B.PROF_CLASSES}
     cnt = {c: sum(s["class_count"][c] for s in stats) for c in B.PROF_CLASSES}
     units = {c: sum(s["class_units"][c] for s in stats) for c in B.PROF_CLASSES}
-    dom = max((c for c in CLASS_COST), key=lambda c: tot[c])
     flops_u, bytes_u, bound, kdt = CLASS_COST[dom]
     nn = n ** 3
     avg_ms = tot[dom] / max(cnt[dom], 1)
@@ -295,7 +304,8 @@ def main():
                  "launches": cnt[dom], "avg_launch_ms": avg_ms,
                  "dof_rhs_per_s": 4 * nn * per_launch_units / (avg_ms * 1e-3),
                  "dof_rhs_per_s_hbm_roofline": hbm * 1e9 / (bytes_u / 4)})
-    class_share = {c: round(tot[c] / max(total_ms / world, 1e-9), 4) for c in B.PROF_CLASSES}
+    step_avg = total_ms / args.steps
+    class_share = {c: round(share_ms[c] / max(step_avg, 1e-9), 4) for c in B.PROF_CLASSES}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -344,8 +354,9 @@ def main():
             "clocks": clocks,
             "detail": {"wall_s": wall, "step_ms": step_ms, "gmres_iters_max": iters,
                        "refinements": [s["refinements"] for s in stats],
-                       "class_ms_per_step": {c: tot[c] / args.steps for c in B.PROF_CLASSES},
-                       "class_share": class_share},
+                       "class_ms_per_step": share_ms, "class_share": class_share,
+                       "class_source": "separate fully profiled pass over the same designs "
+                                       "(untimed); the timed region times only the roofline kernel"},
         }
         print(json.dumps(line), flush=True)
     if world > 1:

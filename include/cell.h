@@ -102,6 +102,11 @@ typedef struct cell_options {
   int const_bank;      /* MIXED: nonzero (default) = FP32 element matrices in one of 4
                           library-wide __constant__ slots (shared by handles with equal
                           matrices), falling back to kernel parameters if all are taken */
+  int graphs;          /* nonzero (default): each GMRES iteration is captured once per
+                          handle into a CUDA graph (on an internal stream) and replayed
+                          on the caller's stream; the first solve pays the capture */
+  int profile_mask;    /* with profile set: bit c (cell_prof_class) = time class c;
+                          0 = every class */
 } cell_options;
 
 typedef struct cell_desc {

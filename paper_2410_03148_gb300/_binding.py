@@ -37,7 +37,7 @@ class cell_options(C.Structure):
         ("vcycles_phi", C.c_int), ("cheb_degree", C.c_int), ("cheb_lo", C.c_double),
         ("cheb_hi", C.c_double), ("schur_shift", C.c_double), ("coarse_dofs", C.c_int),
         ("load_mask", C.c_int), ("profile", C.c_int), ("tensor_cores", C.c_int),
-        ("const_bank", C.c_int),
+        ("const_bank", C.c_int), ("graphs", C.c_int), ("profile_mask", C.c_int),
     ]
 
 

@@ -57,6 +57,12 @@ template <typename T, int NCO, int MODE>
 __device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const NodeIdx& t,
                                          const T* acc, const T* dold) {
 #pragma unroll
+  T c1 = a.c1, c2 = a.c2;
+  if (MODE != AM_LINEAR && a.cc) {
+    c1 = a.cc[0];
+    c2 = a.cc[1];
+  }
+#pragma unroll
   for (int c = 0; c < NCO; ++c) {
     const i64 o = (i64)c * t.nn + t.n;
     if (MODE == AM_LINEAR) {
@@ -68,11 +74,11 @@ __device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const Nod
       a.y[r * a.ys + o] = rr;
       T* sp = a.sol + r * a.ss + o;
       *sp = (a.sol_zero ? T(0) : *sp) + dold[c];
-      if (MODE == AM_CHEB) a.dout[r * a.ds + o] = a.c1 * dold[c] + a.c2 * a.dinv[o] * rr;
+      if (MODE == AM_CHEB) a.dout[r * a.ds + o] = c1 * dold[c] + c2 * a.dinv[o] * rr;
     } else {  // AM_RESID_CHEB0
       const T rr = a.b[r * a.bs + o] - acc[c];
       a.y[r * a.ys + o] = rr;
-      a.dout[r * a.ds + o] = a.c2 * a.dinv[o] * rr;
+      a.dout[r * a.ds + o] = c2 * a.dinv[o] * rr;
     }
   }
 }
@@ -103,10 +109,20 @@ struct ConstCoef {
 // and every coefficient index is a compile-time constant.  Neighbour offsets
 // are 32-bit and each component plane has its own base pointer, so a load is
 // one address multiply-add.
-template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE, typename COEF>
+template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE, int RG,
+          typename COEF>
 __device__ __forceinline__ void apply_fixed_pre_body(const ApplyArgs<T>& a, const COEF& Kc) {
-  const int r = blockIdx.z;
-  if (a.active && !a.active[r]) return;
+  // RG loads per thread share the index arithmetic, the rho loads and every
+  // coefficient fetch; grid z = ceil(nrhs / RG)
+  const int r0 = blockIdx.z * RG;
+  bool on[RG];
+  bool any = false;
+#pragma unroll
+  for (int g = 0; g < RG; ++g) {
+    on[g] = (r0 + g < a.nrhs) && !(a.active && !a.active[r0 + g]);
+    any = any || on[g];
+  }
+  if (!any) return;
   const int nx = a.nx, ny = a.ny;
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= nx * ny) return;
@@ -120,55 +136,74 @@ __device__ __forceinline__ void apply_fixed_pre_body(const ApplyArgs<T>& a, cons
   NodeIdx t;
   t.nn = (i64)nxy * a.nz;
   t.n = (i64)k * nxy + p;
-  const T* X[NCI];
+  T xs[RG][27][NCI];
 #pragma unroll
-  for (int d = 0; d < NCI; ++d) X[d] = a.x + r * a.xs + d * t.nn;
-  T xs[27][NCI];
+  for (int g = 0; g < RG; ++g) {
+    const int r = on[g] ? r0 + g : r0;
+    const T* X[NCI];
 #pragma unroll
-  for (int q = 0; q < 27; ++q) {
-    const int m = xo[q % 3] + yo[(q / 3) % 3] + zo[q / 9];
+    for (int d = 0; d < NCI; ++d) X[d] = a.x + r * a.xs + d * t.nn;
 #pragma unroll
-    for (int d = 0; d < NCI; ++d) xs[q][d] = __ldg(X[d] + m);
+    for (int q = 0; q < 27; ++q) {
+      const int m = xo[q % 3] + yo[(q / 3) % 3] + zo[q / 9];
+#pragma unroll
+      for (int d = 0; d < NCI; ++d) xs[g][q][d] = __ldg(X[d] + m);
+    }
   }
-  T acc[NCO];
+  T acc[RG][NCO];
 #pragma unroll
-  for (int c = 0; c < NCO; ++c) acc[c] = T(0);
+  for (int g = 0; g < RG; ++g)
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) acc[g][c] = T(0);
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
     const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
     const T w = __ldg(a.rho + (xo[ex] + yo[ey] + zo[ez]));
-    T tl[NCO];
+    T tl[RG][NCO];
 #pragma unroll
-    for (int c = 0; c < NCO; ++c) tl[c] = T(0);
+    for (int g = 0; g < RG; ++g)
+#pragma unroll
+      for (int c = 0; c < NCO; ++c) tl[g][c] = T(0);
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const int q = (ex + (b & 1)) + 3 * (ey + ((b >> 1) & 1)) + 9 * (ez + (b >> 2));
 #pragma unroll
       for (int c = 0; c < NCO; ++c)
 #pragma unroll
-        for (int d = 0; d < NCI; ++d)
-          tl[c] = fma(Kc((la * NCM + R0 + c) * (8 * NCM) + b * NCM + C0 + d), xs[q][d], tl[c]);
+        for (int d = 0; d < NCI; ++d) {
+          const T kv = Kc((la * NCM + R0 + c) * (8 * NCM) + b * NCM + C0 + d);
+#pragma unroll
+          for (int g = 0; g < RG; ++g) tl[g][c] = fma(kv, xs[g][q][d], tl[g][c]);
+        }
     }
 #pragma unroll
-    for (int c = 0; c < NCO; ++c) acc[c] = fma(w, tl[c], acc[c]);
-  }
-  if (NEGLAST) acc[NCO - 1] = -acc[NCO - 1];
-  T dold[NCO];
+    for (int g = 0; g < RG; ++g)
 #pragma unroll
-  for (int c = 0; c < NCO; ++c) dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? xs[13][c] : T(0);
-  epilogue<T, NCO, MODE>(a, r, t, acc, dold);
+      for (int c = 0; c < NCO; ++c) acc[g][c] = fma(w, tl[g][c], acc[g][c]);
+  }
+#pragma unroll
+  for (int g = 0; g < RG; ++g) {
+    if (!on[g]) continue;
+    if (NEGLAST) acc[g][NCO - 1] = -acc[g][NCO - 1];
+    T dold[NCO];
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? xs[g][13][c] : T(0);
+    epilogue<T, NCO, MODE>(a, r0 + g, t, acc[g], dold);
+  }
 }
 
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
 __global__ void __launch_bounds__(kBlock)
 k_apply_fixed_pre(const ApplyArgs<T> a, const __grid_constant__ FixedMat<T, NCM> M) {
-  apply_fixed_pre_body<T, NCM, NCI, NCO, R0, C0, NEGLAST, MODE>(a, ParamCoef<T, NCM>{M});
+  apply_fixed_pre_body<T, NCM, NCI, NCO, R0, C0, NEGLAST, MODE, 1>(a, ParamCoef<T, NCM>{M});
 }
 
 template <int SLOT, int NCM, int NCI, int NCO, int R0, int C0, bool NEGLAST, int MODE>
 __global__ void __launch_bounds__(kBlock) k_apply_fixed_cslot(const ApplyArgs<float> a) {
-  apply_fixed_pre_body<float, NCM, NCI, NCO, R0, C0, NEGLAST, MODE>(a, ConstCoef<SLOT, NCM>{});
+  // the single-component (local Schur) operator takes three loads per thread
+  apply_fixed_pre_body<float, NCM, NCI, NCO, R0, C0, NEGLAST, MODE, (NCI == 1 ? 3 : 1)>(
+      a, ConstCoef<SLOT, NCM>{});
 }
 
 // Fixed-matrix operator, FP64: neighbours are loaded per element (FP64
@@ -460,8 +495,11 @@ inline dim3 grid_for(const ApplyArgs<T>& a, int nrhs) {
 }
 
 template <int NCM, int NCI, int NCO, int R0, int C0, bool NEG, int MODE>
-void launch_cslot(const ApplyArgs<float>& a, int nrhs, cudaStream_t s) {
-  const dim3 g = grid_for(a, nrhs);
+void launch_cslot(const ApplyArgs<float>& a0, int nrhs, cudaStream_t s) {
+  constexpr int RG = NCI == 1 ? 3 : 1;
+  ApplyArgs<float> a = a0;
+  a.nrhs = nrhs;
+  const dim3 g = grid_for(a, (nrhs + RG - 1) / RG);
   switch (a.cslot1 - 1) {
     case 0: note_launch(), k_apply_fixed_cslot<0, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
     case 1: note_launch(), k_apply_fixed_cslot<1, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
@@ -473,8 +511,13 @@ void launch_cslot(const ApplyArgs<float>& a, int nrhs, cudaStream_t s) {
 template <typename T, int NCM, int NCI, int NCO, int R0, int C0, bool NEG, int MODE>
 void launch_fixed(const ApplyArgs<T>& a, const FixedMat<T, NCM>& M, int nrhs, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (a.cslot1 > 0) launch_cslot<NCM, NCI, NCO, R0, C0, NEG, MODE>(a, nrhs, s);
-    else note_launch(), k_apply_fixed_pre<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
+    if (a.cslot1 > 0) {
+      launch_cslot<NCM, NCI, NCO, R0, C0, NEG, MODE>(a, nrhs, s);
+    } else {
+      ApplyArgs<T> b = a;
+      b.nrhs = nrhs;
+      note_launch(), k_apply_fixed_pre<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(b, nrhs), kBlock, 0, s>>>(b, M);
+    }
   } else
     note_launch(), k_apply_fixed_ld<T, NCM, NCI, NCO, R0, C0, NEG, MODE><<<grid_for(a, nrhs), kBlock, 0, s>>>(a, M);
 }
@@ -546,7 +589,7 @@ void launch_st(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
 template <typename T, int NC>
 void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
   const long long nn = (long long)a.nx * a.ny * a.nz;
-  if (nn >= 32768) launch_st<T, NC, 3>(a, mode, nrhs, s);
+  if (nn > 65536) launch_st<T, NC, 3>(a, mode, nrhs, s);
   else launch_st<T, NC, 1>(a, mode, nrhs, s);
 }
 

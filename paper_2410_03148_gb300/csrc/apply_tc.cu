@@ -215,6 +215,11 @@ k_apply_tc(const ApplyArgs<float> a, const float* __restrict__ Btiles,
     tc::fence_before_sync();
     __syncthreads();
     // per-node epilogue
+    float c1 = a.c1, c2 = a.c2;
+    if (MODE != AM_LINEAR && a.cc) {
+      c1 = a.cc[0];
+      c2 = a.cc[1];
+    }
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       float av = acc[c * NOWN + t];
@@ -230,11 +235,11 @@ k_apply_tc(const ApplyArgs<float> a, const float* __restrict__ Btiles,
         a.y[r * a.ys + o] = rr;
         float* sp = a.sol + r * a.ss + o;
         *sp = (a.sol_zero ? 0.f : *sp) + dold;
-        if (MODE == AM_CHEB) a.dout[r * a.ds + o] = a.c1 * dold + a.c2 * a.dinv[o] * rr;
+        if (MODE == AM_CHEB) a.dout[r * a.ds + o] = c1 * dold + c2 * a.dinv[o] * rr;
       } else {
         const float rr = a.b[r * a.bs + o] - av;
         a.y[r * a.ys + o] = rr;
-        a.dout[r * a.ds + o] = a.c2 * a.dinv[o] * rr;
+        a.dout[r * a.ds + o] = c2 * a.dinv[o] * rr;
       }
     }
     __syncthreads();  // xs and acc are rewritten by the next load
@@ -246,13 +251,13 @@ k_apply_tc(const ApplyArgs<float> a, const float* __restrict__ Btiles,
 }
 
 template <int NC, int MODE, bool NEG>
+void set_smem_attr() {
+  cudaFuncSetAttribute(k_apply_tc<NC, MODE, NEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, Plan<NC>::SMEM);
+}
+
+template <int NC, int MODE, bool NEG>
 void launch(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cudaStream_t s) {
   using P = Plan<NC>;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_apply_tc<NC, MODE, NEG>, cudaFuncAttributeMaxDynamicSharedMemorySize, P::SMEM);
-    attr = true;
-  }
   const int rg = 3;
   const dim3 g((unsigned)((a.nx / BX) * (a.ny / BY)), (unsigned)(a.nz / BZ), (unsigned)((nrhs + rg - 1) / rg));
   const float* Bt = NC == 3 ? T.b_uu : T.b_full;
@@ -303,6 +308,16 @@ void build_tables(const double* K0, float* btiles, unsigned short* gsrc) {
 }
 
 }  // namespace
+
+// Opt the kernels into their dynamic shared memory (once per device, before
+// any launch or graph capture).
+void tc_prepare() {
+  set_smem_attr<3, AM_LINEAR, false>();
+  set_smem_attr<3, AM_CHEB, false>();
+  set_smem_attr<3, AM_CHEB_LAST, false>();
+  set_smem_attr<3, AM_RESID_CHEB0, false>();
+  set_smem_attr<4, AM_LINEAR, true>();
+}
 
 bool tc_shape_ok(int nx, int ny, int nz) {
   return nx % BX == 0 && ny % BY == 0 && nz % BZ == 0 && nx >= BX && ny >= BY && nz >= BZ;

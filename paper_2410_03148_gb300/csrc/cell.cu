@@ -71,14 +71,26 @@ struct Arena {
   }
 };
 
-// Optional CUDA-event timing of kernel classes (full apply, block applies).
+// Optional CUDA-event timing of kernel classes.  Outside graph capture the
+// events come from a recycled pool; while a GMRES iteration is being captured
+// into a CUDA graph, begin/end create events owned by that graph, which become
+// event-record nodes and are read after every replay of the graph.
+struct GraphMark {
+  int cls;
+  cudaEvent_t e0, e1;
+};
+
 struct Prof {
   bool on = false;
+  unsigned mask = ~0u;  // kernel classes to time
   std::vector<cudaEvent_t> pool;
   std::vector<std::pair<int, int>> marks[CELL_PROF_CLASSES];  // (start, stop) per class
   long long units[CELL_PROF_CLASSES] = {0};
+  double acc_ms[CELL_PROF_CLASSES] = {0};
+  int acc_cnt[CELL_PROF_CLASSES] = {0};
   int cur_units = 9;   // loads processed by the launches being timed
   size_t used = 0;
+  std::vector<GraphMark>* cap = nullptr;  // capture target (graph-owned events)
   cudaEvent_t get() {
     if (used == pool.size()) {
       cudaEvent_t e;
@@ -87,31 +99,62 @@ struct Prof {
     }
     return pool[used++];
   }
-  int begin(cudaStream_t s) {
-    if (!on) return -1;
+  int begin(cudaStream_t s, int cls) {
+    if (!on || !((mask >> cls) & 1u)) return -1;
+    if (cap) {
+      // external records become event-record nodes that timestamp each replay
+      GraphMark m{-1, nullptr, nullptr};
+      cudaEventCreate(&m.e0);
+      cudaEventRecordWithFlags(m.e0, s, cudaEventRecordExternal);
+      cap->push_back(m);
+      return (int)cap->size() - 1;
+    }
     const int i = (int)used;
     cudaEventRecord(get(), s);
     return i;
   }
   void end(int cls, int i0, cudaStream_t s) {
     if (!on || i0 < 0) return;
+    if (cap) {
+      GraphMark& m = (*cap)[i0];
+      m.cls = cls;
+      cudaEventCreate(&m.e1);
+      cudaEventRecordWithFlags(m.e1, s, cudaEventRecordExternal);
+      return;
+    }
     const int i1 = (int)used;
     cudaEventRecord(get(), s);
     marks[cls].push_back({i0, i1});
     units[cls] += cur_units;
   }
+  // after a replay of a graph has completed
+  void add_graph(const std::vector<GraphMark>& gm, int nunits) {
+    for (const GraphMark& m : gm) {
+      if (m.cls < 0) continue;
+      float f = 0.f;
+      if (cudaEventElapsedTime(&f, m.e0, m.e1) != cudaSuccess) {
+        cudaGetLastError();  // timing is best effort; never fail a solve on it
+        continue;
+      }
+      acc_ms[m.cls] += f;
+      acc_cnt[m.cls] += 1;
+      units[m.cls] += nunits;
+    }
+  }
   void collect(double* ms, int* cnt, long long* un) {
     for (int c = 0; c < CELL_PROF_CLASSES; ++c) {
-      double t = 0.0;
+      double t = acc_ms[c];
       for (auto& m : marks[c]) {
         float f = 0.f;
-        cudaEventElapsedTime(&f, pool[m.first], pool[m.second]);
+        if (cudaEventElapsedTime(&f, pool[m.first], pool[m.second]) != cudaSuccess) cudaGetLastError();
         t += f;
       }
       ms[c] = t;
-      cnt[c] = (int)marks[c].size();
+      cnt[c] = (int)marks[c].size() + acc_cnt[c];
       un[c] = units[c];
       units[c] = 0;
+      acc_ms[c] = 0;
+      acc_cnt[c] = 0;
       marks[c].clear();
     }
     used = 0;
@@ -121,6 +164,12 @@ struct Prof {
   }
 };
 
+// One captured GMRES iteration (for a fixed Arnoldi index j).
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<GraphMark> marks;
+  long long nkernels = 0;  // kernels per replay (for cell_launch_count)
+};
 
 template <typename T>
 struct Level {
@@ -131,6 +180,8 @@ struct Level {
   T* dinv = nullptr;     // [NC][nn]
   double lmax = 1.0;
   T *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *d2 = nullptr;  // [9][NC][nn]
+  T* cc = nullptr;       // Chebyshev coefficients on the device: (0, 1/theta), (c1_k, c2_k)
+  int deg = 0;           // Chebyshev steps of this level
   T* dense = nullptr;    // coarsest: regularised inverse (n x n, symmetric)
   int ndense = 0;
   bool coarsest = false;
@@ -143,6 +194,8 @@ struct BlockMG {
   T* fixedm = nullptr;   // device copy of the level-0 element block ((8nc)^2)
   std::vector<double> fixed_host;
   std::vector<T> dense_host;   // staging of the coarsest inverse (kept alive for the async copy)
+  std::vector<T> cc_host;      // staging of the Chebyshev coefficients of all levels
+  T* cc_dev = nullptr;
   unsigned int* lbits = nullptr;  // per-level lambda_max bounds (float bits)
 };
 
@@ -203,6 +256,22 @@ struct cell_handle {
   bool solved = false;
   Prof prof;
   cell_stats last{};
+  // CUDA graphs of the GMRES iterations (one per Arnoldi index), captured on
+  // an internal stream at first use and replayed on the caller's stream
+  std::vector<IterGraph> graphs;
+  cudaStream_t cap_st = nullptr;
+  void free_graphs() {
+    for (IterGraph& g : graphs) {
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      for (GraphMark& m : g.marks) {
+        if (m.e0) cudaEventDestroy(m.e0);
+        if (m.e1) cudaEventDestroy(m.e1);
+      }
+    }
+    graphs.clear();
+    if (cap_st) cudaStreamDestroy(cap_st);
+    cap_st = nullptr;
+  }
 };
 
 namespace {
@@ -231,7 +300,8 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
   a.active = mask;
   a.cslot1 = h->cslot1;
   Krylov<T>& K = kry<T>(h);
-  const int ip = h->prof.begin(h->st);
+  const int pcls = l > 0 ? CELL_PROF_COARSE : (NC == 3 ? CELL_PROF_ELASTIC0 : CELL_PROF_SCHUR0);
+  const int ip = h->prof.begin(h->st, pcls);
   if (l == 0) {
     a.rho = K.rho;
     if constexpr (sizeof(T) == 4 && NC == 3) {
@@ -246,7 +316,7 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
     a.st = L.st;
     cell::apply_stencil<T, NC>(a, mode, 9, h->st);
   }
-  h->prof.end(l > 0 ? CELL_PROF_COARSE : (NC == 3 ? CELL_PROF_ELASTIC0 : CELL_PROF_SCHUR0), ip, h->st);
+  h->prof.end(pcls, ip, h->st);
 }
 
 // Dense assembly of a level's operator on the host (coarsest level only).
@@ -342,6 +412,17 @@ int alloc_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
     CKS(h->arena.alloc(&Lc.dense, (size_t)n * n));
     Lc.ndense = (int)n;
   }
+  // Chebyshev coefficients: 2 (deg + 1) values per level, on the device so
+  // that captured graphs stay valid when a new design changes them
+  const int degc = std::max(8, 4 * o.cheb_degree);
+  const int stride = 2 * (degc + 1);
+  CKS(h->arena.alloc(&mg.cc_dev, (size_t)stride * nl));
+  mg.cc_host.assign((size_t)stride * nl, T(0));
+  for (int l = 0; l < nl; ++l) {
+    Level<T>& L = mg.lv[l];
+    L.cc = mg.cc_dev + (size_t)stride * l;
+    L.deg = (L.coarsest && !L.dense) ? degc : o.cheb_degree;
+  }
   return CELL_OK;
 }
 
@@ -394,51 +475,51 @@ int fill_mg(cell_handle* h, BlockMG<T>& mg) {
     std::memcpy(&lf, &bits[l], sizeof(float));
     mg.lv[l].lmax = lf > 0 ? (double)lf : 1.0;
   }
+  const cell_options& o = h->d.opt;
+  const size_t stride = mg.cc_host.size() / nl;
+  for (int l = 0; l < nl; ++l) {
+    const double hi = mg.lv[l].lmax * o.cheb_hi, lo = hi * o.cheb_lo;
+    const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+    T* c = mg.cc_host.data() + stride * l;
+    c[0] = T(0);
+    c[1] = (T)(1.0 / theta);
+    double rp = 1.0 / sigma;
+    for (int k = 1; k < mg.lv[l].deg; ++k) {
+      const double rk = 1.0 / (2.0 * sigma - rp);
+      c[2 * k] = (T)(rk * rp);
+      c[2 * k + 1] = (T)(2.0 * rk / delta);
+      rp = rk;
+    }
+  }
+  CK(cudaMemcpyAsync(mg.cc_dev, mg.cc_host.data(), mg.cc_host.size() * sizeof(T), cudaMemcpyHostToDevice,
+                     h->st));
   return CELL_OK;
 }
 
-struct ChebCoef {
-  double theta, delta, sigma, rho0;
-};
-
-inline ChebCoef cheb_coef(const cell_options& o, double lmax) {
-  const double hi = lmax * o.cheb_hi, lo = hi * o.cheb_lo;
-  ChebCoef c;
-  c.theta = 0.5 * (hi + lo);
-  c.delta = 0.5 * (hi - lo);
-  c.sigma = c.theta / c.delta;
-  c.rho0 = 1.0 / c.sigma;
-  return c;
-}
-
-// x = V-cycle approximation of A_l^-1 b (zero initial guess).
+// x = V-cycle approximation of A_l^-1 b (zero initial guess).  Chebyshev
+// coefficients are read from the level's device table (see fill_mg).
 template <typename T, int NC>
 void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64 xs, const int* mask) {
-  const cell_options& o = h->d.opt;
   Level<T>& L = mg.lv[l];
   const i64 ws = NC * L.nn;
   if (L.coarsest && L.dense) {
     cell::dense_solve<T>(L.dense, L.ndense, b, bs, x, xs, L.nn, NC, 9, mask, h->st);
     return;
   }
-  const int deg = L.coarsest ? std::max(8, 4 * o.cheb_degree) : o.cheb_degree;
-  const ChebCoef cc = cheb_coef(o, L.lmax);
+  const int deg = L.deg;
   cell::ApplyArgs<T> a{};
   // pre-smoothing from x = 0
-  cell::cheb_init<T, NC>(b, bs, L.r, ws, L.d, ws, L.dinv, (T)(1.0 / cc.theta), L.nn, 9, mask, h->st);
-  double rp = cc.rho0;
+  cell::cheb_init<T, NC>(b, bs, L.r, ws, L.d, ws, L.dinv, L.cc + 1, L.nn, 9, mask, h->st);
   T* d = L.d;
   T* d2 = L.d2;
   int zero = 1;
   for (int k = 1; k < deg; ++k) {
-    const double rk = 1.0 / (2.0 * cc.sigma - rp);
     a = cell::ApplyArgs<T>{};
     a.x = d; a.xs = ws; a.y = L.r; a.ys = ws; a.sol = x; a.ss = xs; a.dout = d2; a.ds = ws;
-    a.c1 = (T)(rk * rp); a.c2 = (T)(2.0 * rk / cc.delta); a.sol_zero = zero;
+    a.cc = L.cc + 2 * k; a.sol_zero = zero;
     level_apply<T, NC>(h, mg, l, cell::AM_CHEB, a, mask);
     std::swap(d, d2);
     zero = 0;
-    rp = rk;
   }
   a = cell::ApplyArgs<T>{};
   a.x = d; a.xs = ws; a.y = L.r; a.ys = ws; a.sol = x; a.ss = xs; a.sol_zero = zero;
@@ -452,19 +533,16 @@ void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64
   // post-smoothing
   a = cell::ApplyArgs<T>{};
   a.x = x; a.xs = xs; a.b = b; a.bs = bs; a.y = L.r; a.ys = ws; a.dout = L.d; a.ds = ws;
-  a.c2 = (T)(1.0 / cc.theta);
+  a.cc = L.cc;
   level_apply<T, NC>(h, mg, l, cell::AM_RESID_CHEB0, a, mask);
-  rp = cc.rho0;
   d = L.d;
   d2 = L.d2;
   for (int k = 1; k < deg; ++k) {
-    const double rk = 1.0 / (2.0 * cc.sigma - rp);
     a = cell::ApplyArgs<T>{};
     a.x = d; a.xs = ws; a.y = L.r; a.ys = ws; a.sol = x; a.ss = xs; a.dout = d2; a.ds = ws;
-    a.c1 = (T)(rk * rp); a.c2 = (T)(2.0 * rk / cc.delta); a.sol_zero = 0;
+    a.cc = L.cc + 2 * k; a.sol_zero = 0;
     level_apply<T, NC>(h, mg, l, cell::AM_CHEB, a, mask);
     std::swap(d, d2);
-    rp = rk;
   }
   cell::axpy_view<T, NC>(x, xs, d, ws, L.nn, 9, mask, h->st);
 }
@@ -495,7 +573,7 @@ void precond(cell_handle* h, const T* v, T* z, const int* mask) {
   a.alpha = T(1); a.beta = T(1); a.rho = K.rho; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
   a.active = mask;
   a.cslot1 = h->cslot1;
-  const int ip = h->prof.begin(h->st);
+  const int ip = h->prof.begin(h->st, CELL_PROF_COUPLING);
   cell::apply_pu<T>(a, K.K0, 9, h->st);
   h->prof.end(CELL_PROF_COUPLING, ip, h->st);
   block_solve<T, 1>(h, K.mgp, h->d.opt.vcycles_phi, K.tphi, nn, z + 3 * nn, len, K.rp, K.ep, mask);
@@ -508,14 +586,15 @@ void apply_full_T(cell_handle* h, const T* x, i64 xs, T* y, i64 ys, const T* b, 
   a.x = x; a.xs = xs; a.y = y; a.ys = ys; a.b = b; a.bs = bs; a.alpha = alpha; a.beta = beta;
   a.rho = rho_of<T>(h); a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.active = mask;
   a.cslot1 = h->cslot1;
-  const int ip = h->prof.begin(h->st);
+  const int pcls = sizeof(T) == 4 ? CELL_PROF_FULL32 : CELL_PROF_FULL64;
+  const int ip = h->prof.begin(h->st, pcls);
   if constexpr (sizeof(T) == 4) {
     if (h->tc_ok && h->d.opt.tensor_cores >= 2) cell::apply_tc_full(a, h->tct, nrhs, h->tc_err, h->st);
     else cell::apply_full<T>(a, h->kf.K0, cell::AM_LINEAR, nrhs, h->st);
   } else {
     cell::apply_full<T>(a, h->kd.K0, cell::AM_LINEAR, nrhs, h->st);
   }
-  h->prof.end(sizeof(T) == 4 ? CELL_PROF_FULL32 : CELL_PROF_FULL64, ip, h->st);
+  h->prof.end(pcls, ip, h->st);
 }
 
 template <typename T>
@@ -558,6 +637,43 @@ int fill_krylov(cell_handle* h) {
   return CELL_OK;
 }
 
+// One Arnoldi step j of the batched GMRES (all kernels, no host sync):
+// z = P^-1 v_j, w = Ahat z, Gram-Schmidt against v_0..v_j, Givens update,
+// normalisation.  Launches go to h->st (the capture stream while captured).
+template <typename T>
+void iteration(cell_handle* h, int j) {
+  Krylov<T>& K = kry<T>(h);
+  const int m = K.m;
+  const i64 len = K.len;
+  const i64 vstride = 9 * len;
+  cudaStream_t s = h->st;
+  const int nblk = h->nblk;
+  T* vj = K.V + (i64)j * vstride;
+  T* w = K.V + (i64)(j + 1) * vstride;
+  precond<T>(h, vj, K.z, h->active);
+  apply_full_T<T>(h, K.z, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
+  // Classical Gram-Schmidt with selective reorthogonalisation: one pass of
+  // dots (w is V_{j+1}, so the same pass also gives |w|^2), one update with
+  // the new norm, and a second pass only for loads whose norm dropped below
+  // 1/sqrt(2) of its value before the pass.
+  const int ipk = h->prof.begin(s, CELL_PROF_KRYLOV);
+  cell::multidot<T>(K.V, vstride, len, j + 2, w, len, len, h->partial, nblk, kNvMax, 9, h->active, s);
+  cell::reduce_partials(h->partial, nblk, j + 2, kNvMax, h->hcol, 0, 9, h->active, s);
+  cell::update<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->active, s);
+  cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->active, s);
+  cell::reorth_flag(h->hcol, h->hnorm, j, h->active, h->reorth, 9, s);
+  cell::multidot<T>(K.V, vstride, len, j + 1, w, len, len, h->partial, nblk, kNvMax, 9, h->reorth, s);
+  cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->ybuf, 0, 9, h->reorth, s);
+  cell::update<T>(K.V, vstride, len, j + 1, h->ybuf, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->reorth, s);
+  cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->reorth, s);
+  // hcol += second-pass coefficients (a one-block "reduction" of ybuf)
+  cell::reduce_partials(h->ybuf, 1, j + 1, kNvMax, h->hcol, 1, 9, h->reorth, s);
+  h->prof.end(CELL_PROF_KRYLOV, ipk, s);
+  cell::givens_step(h->H, h->cs, h->sn, h->g, h->hcol, h->hnorm, j, m, h->active, h->resid,
+                    h->tolabs, h->invscale, h->kcount, 9, s);
+  cell::scale_vec<T>(w, len, len, h->invscale, 9, s);
+}
+
 // One restarted GMRES cycle (<= m iterations) on Ahat d = r64 for the loads
 // in h->want, in precision T; on return x64 += d.
 template <typename T>
@@ -587,42 +703,58 @@ int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
   for (int q = 0; q < 9; ++q) nran += ran[q] ? 1 : 0;
   if (!nran) return CELL_OK;
   h->prof.cur_units = nran;
+  const bool graphs = h->d.opt.graphs != 0;
+  if (graphs && h->graphs.empty()) {
+    h->graphs.resize(m);
+    CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  }
   int j = 0;
+  int nunits = nran;
   for (; j < m; ++j) {
-    T* vj = K.V + (i64)j * vstride;
-    T* w = K.V + (i64)(j + 1) * vstride;
-    precond<T>(h, vj, K.z, h->active);
-    apply_full_T<T>(h, K.z, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
-    // Classical Gram-Schmidt with selective reorthogonalisation: one pass of
-    // dots (w is V_{j+1}, so the same pass also gives |w|^2), one update with
-    // the new norm, and a second pass only for loads whose norm dropped below
-    // 1/sqrt(2) of its value before the pass.
-    const int ipk = h->prof.begin(s);
-    cell::multidot<T>(K.V, vstride, len, j + 2, w, len, len, h->partial, nblk, kNvMax, 9, h->active, s);
-    cell::reduce_partials(h->partial, nblk, j + 2, kNvMax, h->hcol, 0, 9, h->active, s);
-    cell::update<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->active, s);
-    cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->active, s);
-    cell::reorth_flag(h->hcol, h->hnorm, j, h->active, h->reorth, 9, s);
-    cell::multidot<T>(K.V, vstride, len, j + 1, w, len, len, h->partial, nblk, kNvMax, 9, h->reorth, s);
-    cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->ybuf, 0, 9, h->reorth, s);
-    cell::update<T>(K.V, vstride, len, j + 1, h->ybuf, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->reorth, s);
-    cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->reorth, s);
-    // hcol += second-pass coefficients (a one-block "reduction" of ybuf)
-    cell::reduce_partials(h->ybuf, 1, j + 1, kNvMax, h->hcol, 1, 9, h->reorth, s);
-    h->prof.end(CELL_PROF_KRYLOV, ipk, s);
-    cell::givens_step(h->H, h->cs, h->sn, h->g, h->hcol, h->hnorm, j, m, h->active, h->resid,
-                      h->tolabs, h->invscale, h->kcount, 9, s);
-    cell::scale_vec<T>(w, len, len, h->invscale, 9, s);
+    if (graphs) {
+      IterGraph& G = h->graphs[j];
+      if (!G.exec) {
+        // capture this iteration once: launches go to the capture stream
+        cudaStream_t user = h->st;
+        h->st = h->cap_st;
+        h->prof.cap = &G.marks;
+        cudaGraph_t graph = nullptr;
+        const long long n0 = cell::g_launches.load();
+        cudaError_t e = cudaStreamBeginCapture(h->cap_st, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+          iteration<T>(h, j);
+          e = cudaStreamEndCapture(h->cap_st, &graph);
+        }
+        // captured launches run at each replay, not now
+        G.nkernels = cell::g_launches.load() - n0;
+        cell::g_launches.fetch_sub(G.nkernels);
+        h->prof.cap = nullptr;
+        h->st = user;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+          set_error("CUDA graph capture of a GMRES iteration", e);
+          return CELL_ECUDA;
+        }
+      }
+      CK(cudaGraphLaunch(G.exec, s));
+      cell::g_launches.fetch_add(G.nkernels);
+    } else {
+      iteration<T>(h, j);
+    }
     int act[9];
     CK(cudaMemcpyAsync(act, h->active, sizeof(act), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (graphs && h->prof.on) h->prof.add_graph(h->graphs[j].marks, nunits);
     int nact = 0;
     for (int q = 0; q < 9; ++q) nact += act[q] ? 1 : 0;
     if (!nact) break;
     h->prof.cur_units = nact;
+    nunits = nact;
   }
   h->prof.cur_units = nran;
   cell::backsolve(h->H, h->g, h->kcount, m, h->ybuf, 9, h->ranmask, s);
+
   cell::lincomb<T>(K.V, vstride, len, h->ybuf, h->kcount, kNvMax, K.u, len, len, 9, h->ranmask, s);
   precond<T>(h, K.u, K.z, h->ranmask);
   if constexpr (sizeof(T) == 4)
@@ -705,6 +837,7 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   h->nn = (i64)d->nx * d->ny * d->nz;
   h->st = static_cast<cudaStream_t>(d->stream);
   h->prof.on = d->opt.profile != 0;
+  h->prof.mask = d->opt.profile_mask ? (unsigned)d->opt.profile_mask : ~0u;
   cellhost::nondimensionalise(d->C, d->e, d->kappa, h->Cn, h->en, h->kn, &h->C0, &h->k0);
   h->h[0] = 1.0 / d->nx;
   h->h[1] = 1.0 / d->ny;
@@ -747,6 +880,7 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st));
   h->tc_ok = cell::tc_shape_ok(h->nx, h->ny, h->nz);
   if (h->tc_ok) {
+    cell::tc_prepare();
     std::vector<float> bu(cell::tc_table_floats(3)), bf(cell::tc_table_floats(4));
     std::vector<unsigned short> gu(cell::tc_table_idx(3)), gf(cell::tc_table_idx(4));
     cell::tc_build_tables_host(h->K0, bu.data(), gu.data(), bf.data(), gf.data());
@@ -774,7 +908,8 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(A.alloc(&h->r64, 9 * len));
   CKS(A.alloc(&h->xh, 9 * len));
   CKS(A.alloc(&h->xl, 9 * len));
-  h->nblk = (int)std::min<i64>(1024, std::max<i64>(1, (len + 4095) / 4096));
+  // blocks per load of the reductions: ~8192 entries per block (32 per thread)
+  h->nblk = (int)std::min<i64>(1024, std::max<i64>(1, (len + 8191) / 8192));
   CKS(A.alloc(&h->partial, (size_t)9 * 4 * h->nblk * kNvMax));
   CKS(A.alloc(&h->red, 9 * kNvMax));
   CKS(A.alloc(&h->red2, 9 * kNvMax));
@@ -870,7 +1005,7 @@ int solve_impl(cell_handle* h, cell_stats* st) {
     // FP64-grade residual of the updated iterate: r = bhat - Ahat x
     h->prof.cur_units = 9;
     if constexpr (sizeof(T) == 4) {
-      const int ip = h->prof.begin(s);
+      const int ip = h->prof.begin(s, CELL_PROF_FULL64);
       cell::resid_df(h->xh, h->xl, len, h->b64, len, h->r64, len, h->rho32, h->rho_l, h->DF,
                      h->nx, h->ny, h->nz, 9, nullptr, s);
       h->prof.end(CELL_PROF_FULL64, ip, s);
@@ -931,6 +1066,8 @@ void cell_default_options(cell_options* o) {
   o->profile = 0;
   o->tensor_cores = 0;
   o->const_bank = 1;
+  o->graphs = 1;
+  o->profile_mask = 0;
 }
 
 int cell_setup(const cell_desc* d, cell_handle** out) {
@@ -1146,6 +1283,7 @@ int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]) {
 void cell_destroy(cell_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  h->free_graphs();
   cell::cslot_release(h->cslot1);
   h->arena.release();
   delete h;

@@ -62,10 +62,12 @@ struct ApplyArgs {
   const T* ke;             // per-element matrices, SoA: ke[entry*ne + e]
   const T* st;             // assembled 27-point block stencil, SoA: st[((q*NC+c)*NC+d)*nn + n]
   T alpha, beta, c1, c2;
+  const T* cc;             // if set: device (c1, c2) pair used instead of c1, c2
   int nx, ny, nz;
   int sol_zero;            // CHEB modes: incoming sol is implicitly zero
   const int* active;       // per-rhs flag (nullptr = all active)
   int cslot1;              // FP32 fixed-matrix kernels: constant-bank slot + 1 (0 = use parameter)
+  int nrhs;                // number of loads of the launch (set by the launchers)
 };
 
 // Constant-bank slots holding (K0, S0) in FP32 for the fixed-matrix kernels;
@@ -124,6 +126,7 @@ struct TcTables {
   const unsigned short* g_full = nullptr;
 };
 bool tc_shape_ok(int nx, int ny, int nz);
+void tc_prepare();
 size_t tc_table_floats(int nc);
 size_t tc_table_idx(int nc);
 void tc_build_tables_host(const double* K0, float* b_uu, unsigned short* g_uu, float* b_full,
@@ -133,8 +136,9 @@ void apply_tc_uu(const ApplyArgs<float>& a, const TcTables& T, int mode, int nrh
 void apply_tc_full(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cudaStream_t s);
 
 // ---- multigrid helpers (mg.cu) ----------------------------------------------
+// r = b, d = c2 Dinv b with c2 read from device memory (*c2p)
 template <typename T, int NC> void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds,
-                                             const T* dinv, T c2, i64 nn, int nrhs,
+                                             const T* dinv, const T* c2p, i64 nn, int nrhs,
                                              const int* active, cudaStream_t s);
 template <typename T, int NC> void axpy_view(T* x, i64 xs, const T* d, i64 ds, i64 nn, int nrhs,
                                              const int* active, cudaStream_t s);

@@ -16,12 +16,13 @@ inline unsigned nblocks(i64 n, int b = kB) { return (unsigned)((n + b - 1) / b);
 
 template <typename T, int NC>
 __global__ void k_cheb_init(const T* __restrict__ b, i64 bs, T* __restrict__ r, i64 rs,
-                            T* __restrict__ d, i64 ds, const T* __restrict__ dinv, T c2, i64 nn,
-                            const int* active) {
+                            T* __restrict__ d, i64 ds, const T* __restrict__ dinv,
+                            const T* __restrict__ c2p, i64 nn, const int* active) {
   const int q = blockIdx.y;
   if (active && !active[q]) return;
   const i64 n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
+  const T c2 = *c2p;
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
     const T v = b[q * bs + c * nn + n];
@@ -251,9 +252,9 @@ __global__ void k_dense_solve(const T* __restrict__ Ainv, int n, const T* __rest
 }  // namespace
 
 template <typename T, int NC>
-void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds, const T* dinv, T c2, i64 nn,
+void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds, const T* dinv, const T* c2p, i64 nn,
                int nrhs, const int* active, cudaStream_t s) {
-  note_launch(), k_cheb_init<T, NC><<<dim3(nblocks(nn), nrhs), kB, 0, s>>>(b, bs, r, rs, d, ds, dinv, c2, nn, active);
+  note_launch(), k_cheb_init<T, NC><<<dim3(nblocks(nn), nrhs), kB, 0, s>>>(b, bs, r, rs, d, ds, dinv, c2p, nn, active);
 }
 template <typename T, int NC>
 void axpy_view(T* x, i64 xs, const T* d, i64 ds, i64 nn, int nrhs, const int* active, cudaStream_t s) {
@@ -296,7 +297,7 @@ void dense_solve(const T* Ainv, int n, const T* b, i64 bs, T* x, i64 xs, i64 nn,
 }
 
 #define INST_NC(T, NC)                                                                              \
-  template void cheb_init<T, NC>(const T*, i64, T*, i64, T*, i64, const T*, T, i64, int, const int*, \
+  template void cheb_init<T, NC>(const T*, i64, T*, i64, T*, i64, const T*, const T*, i64, int, const int*, \
                                  cudaStream_t);                                                     \
   template void axpy_view<T, NC>(T*, i64, const T*, i64, i64, int, const int*, cudaStream_t);        \
   template void restrict_fw<T, NC>(const T*, i64, T*, i64, int, int, int, int, const int*,          \

@@ -295,6 +295,34 @@ def test_constant_bank_and_parameter_kernels_agree():
         assert np.abs(a - b).max() <= 1e-10 * np.abs(b).max()
 
 
+def test_graphs_and_direct_launches_agree():
+    """Replaying captured GMRES iterations gives bitwise the same solve as
+    launching them directly, across designs (graphs survive cell_update)."""
+    designs = [cellgen.gaussian_levelset(16, seed=s) for s in (21, 22)]
+    res = {}
+    for g in (0, 1):
+        cell = make_cell(designs[0], "phi", graphs=g)
+        out = []
+        for d in designs:
+            cell.update(torch.as_tensor(d, device=dev()))
+            st = cell.solve()
+            out.append((st["iters"], np.concatenate([a.ravel() for a in cell.homogenise()])))
+        res[g] = out
+        cell.close()
+    for (i0, h0), (i1, h1) in zip(res[0], res[1]):
+        assert i0 == i1
+        assert np.array_equal(h0, h1)
+
+
+def test_profiled_graph_solve_reports_kernel_times():
+    phi = cellgen.gaussian_levelset(16, seed=23)
+    cell = make_cell(phi, "phi", graphs=1, profile=1)
+    for _ in range(2):
+        st = cell.solve()
+        assert st["class_count"]["full32"] > 0 and st["class_ms"]["full32"] > 0
+        assert st["class_ms"]["elastic0"] > 0 and st["class_units"]["elastic0"] > 0
+
+
 def test_update_equals_fresh_setup():
     """cell_update on a handle reproduces a fresh cell_setup bitwise."""
     a, b = (cellgen.gaussian_levelset(16, seed=s) for s in (11, 12))
