@@ -72,8 +72,14 @@ typedef enum cell_dtype {
   CELL_F32 = 0,
   CELL_F64 = 1,
   CELL_F64_DF = 2,  /* FP64 data, arithmetic in FP32 pairs (cell_apply only) */
-  CELL_F32_TC = 3   /* FP32 data, TF32 tensor-core element contraction (cell_apply only) */
+  CELL_F32_TC = 3   /* FP32 data, TF32 tensor-core element contraction (cell_apply,
+                       cell_apply_block) */
 } cell_dtype;
+
+typedef enum cell_block {
+  CELL_BLOCK_A = 0,     /* elastic block A of the coupled operator */
+  CELL_BLOCK_SBAR = 1   /* element-wise Schur approximation Sbar */
+} cell_block;
 
 typedef struct cell_options {
   double tol;          /* stop when ||r_I||_2 <= tol * ||b_I||_2 for every load I
@@ -95,10 +101,12 @@ typedef struct cell_options {
   int coarse_dofs;     /* stop coarsening once a level has at most this many dofs */
   int load_mask;       /* bit I set = solve load I (default 0x1FF = all nine) */
   int profile;         /* nonzero: time kernel classes with CUDA events (cell_stats) */
-  int tensor_cores;    /* MIXED: 0 = SIMT FP32 applies only (default); 1 = fine-grid elastic
-                          smoothing applies on tcgen05 tensor cores (TF32 element
-                          contraction, FP32 accumulate); 2 = also the Krylov operator.
-                          Used where nx % 16 == 0, ny % 4 == 0, nz % 2 == 0. */
+  int tensor_cores;    /* MIXED: 0 = SIMT FP32 applies only; 1 = fine-grid smoothing applies
+                          of both preconditioner blocks (A and Sbar) on tcgen05 tensor
+                          cores (TF32 element contraction, FP32 accumulate), used where
+                          nx % 8 == 0 and nx <= 128; 2 = also the Krylov operator Ahat
+                          (3xTF32 split, FP32-accurate), used where nx % 16 == 0,
+                          ny % 4 == 0, nz % 2 == 0. */
   int const_bank;      /* MIXED: nonzero (default) = FP32 element matrices in one of 4
                           library-wide __constant__ slots (shared by handles with equal
                           matrices), falling back to kernel parameters if all are taken */
@@ -175,7 +183,8 @@ int cell_update(cell_handle* h, const void* input);
 /* Solve the selected cell problems (§2.2) for the design of the handle:
  * assemble b = -sum_e rho_e P_e^T K0 Zbar_e (negated potential rows, the
  * nonsymmetric form of Eq. (sym-piezo)), run right-preconditioned SCP-GMRES
- * (§2.5.3), and project the null space (mean displacement and potential) out
+ * (§2.5.3, flexible variant: the preconditioned directions are stored, so
+ * reduced-precision smoothers may vary between iterations), and project the null space (mean displacement and potential) out
  * of the solutions.  st may be NULL.  Returns CELL_ENOTCONV (with stats and a
  * usable best solution) if tol was not reached within max_iter/max_refine. */
 int cell_solve(cell_handle* h, cell_stats* st);
@@ -218,6 +227,16 @@ int cell_get_solution(cell_handle* h, double* out);
  * inputs, FP32 accumulation); CELL_EINVAL if the grid does not tile into
  * 16 x 4 x 2 node bricks. */
 int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype);
+
+/* Preconditioner blocks of P_SCP (§2.5.3) on the finest grid: y = A x with
+ * block CELL_BLOCK_A (the elastic block of Eq. (sym-piezo), sum_e rho_e A_e,
+ * 3 components per node) or y = Sbar x with CELL_BLOCK_SBAR (sum_e rho_e S0,
+ * S0 = C_e + B_e (A_e + shift I)^-1 B_e^T, 1 component).  x, y: device,
+ * nrhs vectors of [comp][node] (3nn or nn values each), not aliased.
+ * dtype CELL_F32 / CELL_F64: SIMT; CELL_F32_TC: the z-marching tensor-core
+ * kernel used by the smoothers (TF32 inputs, FP32 accumulation; CELL_EINVAL
+ * unless nx % 8 == 0 and nx <= 128).  Asynchronous on the handle's stream. */
+int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs, int dtype);
 
 /* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as
  * FP64 cell vectors into the DEVICE buffer out (9*4*N values). */

@@ -20,11 +20,12 @@ CELL_OK, CELL_EINVAL, CELL_ENOMEM, CELL_ENOTCONV, CELL_ETIMEOUT, CELL_ECUDA, CEL
 CELL_FP64, CELL_MIXED_FP32 = 0, 1
 CELL_INPUT_RHO, CELL_INPUT_PHI = 0, 1
 CELL_F32, CELL_F64, CELL_F64_DF, CELL_F32_TC = 0, 1, 2, 3
+CELL_BLOCK_A, CELL_BLOCK_SBAR = 0, 1
 
 # every symbol include/cell.h declares
 EXPORTS = [
     "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_homogenise", "cell_sensitivity",
-    "cell_dh", "cell_get_solution", "cell_apply", "cell_rhs", "cell_get_rho",
+    "cell_dh", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
     "cell_element_matrices", "cell_homogenise_noalloc", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
 ]
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.cell_dh.argtypes = [D, D, D, D, D]
     lib.cell_get_solution.argtypes = [P, P]
     lib.cell_apply.argtypes = [P, P, P, C.c_int, C.c_int]
+    lib.cell_apply_block.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
     lib.cell_rhs.argtypes = [P, P]
     lib.cell_get_rho.argtypes = [P, P]
     lib.cell_element_matrices.argtypes = [C.POINTER(cell_desc), D, D]
@@ -223,6 +225,11 @@ def cell_get_solution(h, out_ptr: int):
 
 def cell_apply(h, x_ptr: int, y_ptr: int, nrhs: int, dtype: int):
     _check("cell_apply", load().cell_apply(h, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nrhs, dtype))
+
+
+def cell_apply_block(h, block: int, x_ptr: int, y_ptr: int, nrhs: int, dtype: int):
+    _check("cell_apply_block",
+           load().cell_apply_block(h, block, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nrhs, dtype))
 
 
 def cell_rhs(h, out_ptr: int):

@@ -86,6 +86,19 @@ class Cell:
                      B.CELL_F32 if x.dtype == torch.float32 else B.CELL_F64)
         return y
 
+    def apply_block(self, block: str, x: torch.Tensor, tensor_cores: bool = False) -> torch.Tensor:
+        """y = A x (block "A", x of shape (nrhs, 3, nz, ny, nx)) or y = Sbar x
+        (block "Sbar", shape (nrhs, 1, nz, ny, nx)): the preconditioner blocks."""
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        if tensor_cores:
+            dt = B.CELL_F32_TC
+        else:
+            dt = B.CELL_F32 if x.dtype == torch.float32 else B.CELL_F64
+        blk = B.CELL_BLOCK_A if block == "A" else B.CELL_BLOCK_SBAR
+        B.cell_apply_block(self._h, blk, x.data_ptr(), y.data_ptr(), x.shape[0], dt)
+        return y
+
     def rhs(self) -> torch.Tensor:
         out = torch.empty((9, 4) + self.shape, dtype=torch.float64, device=self.device)
         B.cell_rhs(self._h, out.data_ptr())

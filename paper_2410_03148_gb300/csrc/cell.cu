@@ -204,7 +204,7 @@ struct Krylov {
   int m = 0;
   i64 len = 0;
   T* V = nullptr;        // (m+1) x 9 x len
-  T* z = nullptr;        // 9 x len
+  T* Z = nullptr;        // m x 9 x len: preconditioned directions z_j = P^-1 v_j (flexible GMRES)
   T* u = nullptr;        // 9 x len
   T* tphi = nullptr;     // 9 x nn (Schur block right-hand side)
   T* ru = nullptr;       // 9 x 3nn (extra elastic V-cycles)
@@ -238,6 +238,8 @@ struct cell_handle {
   int* bad = nullptr;
   int* tc_err = nullptr;   // tensor-core kernels: expired bounded waits
   bool tc_ok = false;      // grid tiles into tensor-core bricks
+  bool zm_ok = false;      // grid suits the z-marching tensor-core smoothers
+  float* zb = nullptr;     // their B operands: [ZK_UU | ZK_PP4][1024]
   cell::TcTables tct;      // tensor-core operand tables (device)
   int cslot1 = 0;          // constant-bank slot of the FP32 element matrices (+1)
   cell::DFMat DF;
@@ -304,9 +306,15 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
   const int ip = h->prof.begin(h->st, pcls);
   if (l == 0) {
     a.rho = K.rho;
-    if constexpr (sizeof(T) == 4 && NC == 3) {
-      if (h->tc_ok && h->d.opt.tensor_cores >= 1) cell::apply_tc_uu(a, h->tct, mode, 9, h->tc_err, h->st);
-      else cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
+    if constexpr (sizeof(T) == 4) {
+      if (h->zm_ok && h->d.opt.tensor_cores >= 1) {
+        const int kind = NC == 3 ? cell::ZK_UU : cell::ZK_PP4;
+        cell::apply_zmarch(kind, a, h->zb + 1024 * kind, mode, 9, h->tc_err, h->st);
+      } else if constexpr (NC == 3) {
+        cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
+      } else {
+        cell::apply_ss<T>(a, K.S0, mode, 9, h->st);
+      }
     } else if constexpr (NC == 3) {
       cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
     } else {
@@ -607,7 +615,7 @@ int setup_krylov(cell_handle* h) {
   for (int i = 0; i < 1024; ++i) K.K0.k[i] = (T)h->K0[i];
   for (int i = 0; i < 64; ++i) K.S0.k[i] = (T)h->S0[i];
   CKS(h->arena.alloc(&K.V, (size_t)(K.m + 1) * 9 * K.len));
-  CKS(h->arena.alloc(&K.z, (size_t)9 * K.len));
+  CKS(h->arena.alloc(&K.Z, (size_t)K.m * 9 * K.len));
   CKS(h->arena.alloc(&K.u, (size_t)9 * K.len));
   CKS(h->arena.alloc(&K.tphi, (size_t)9 * h->nn));
   if (o.vcycles_u > 1) {
@@ -650,8 +658,9 @@ void iteration(cell_handle* h, int j) {
   const int nblk = h->nblk;
   T* vj = K.V + (i64)j * vstride;
   T* w = K.V + (i64)(j + 1) * vstride;
-  precond<T>(h, vj, K.z, h->active);
-  apply_full_T<T>(h, K.z, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
+  T* zj = K.Z + (i64)j * vstride;
+  precond<T>(h, vj, zj, h->active);
+  apply_full_T<T>(h, zj, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
   // Classical Gram-Schmidt with selective reorthogonalisation: one pass of
   // dots (w is V_{j+1}, so the same pass also gives |w|^2), one update with
   // the new norm, and a second pass only for loads whose norm dropped below
@@ -755,12 +764,13 @@ int gmres_cycle(cell_handle* h, const double* tolabs_host, int* iters) {
   h->prof.cur_units = nran;
   cell::backsolve(h->H, h->g, h->kcount, m, h->ybuf, 9, h->ranmask, s);
 
-  cell::lincomb<T>(K.V, vstride, len, h->ybuf, h->kcount, kNvMax, K.u, len, len, 9, h->ranmask, s);
-  precond<T>(h, K.u, K.z, h->ranmask);
+  // flexible GMRES: d = Z y with the stored preconditioned directions, so the
+  // preconditioner may vary between iterations (reduced-precision smoothers)
+  cell::lincomb<T>(K.Z, vstride, len, h->ybuf, h->kcount, kNvMax, K.u, len, len, 9, h->ranmask, s);
   if constexpr (sizeof(T) == 4)
-    cell::axpy_split<T>(h->x64, h->xh, h->xl, len, K.z, len, len, h->ones, 9, h->ranmask, s);
+    cell::axpy_split<T>(h->x64, h->xh, h->xl, len, K.u, len, len, h->ones, 9, h->ranmask, s);
   else
-    cell::axpy_f64<T>(h->x64, len, K.z, len, len, h->ones, 9, h->ranmask, s);
+    cell::axpy_f64<T>(h->x64, len, K.u, len, len, h->ones, 9, h->ranmask, s);
   int kc[9];
   CK(cudaMemcpyAsync(kc, h->kcount, sizeof(kc), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
@@ -898,6 +908,15 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
     h->tct.b_full = dbf;
     h->tct.g_uu = dgu;
     h->tct.g_full = dgf;
+  }
+  h->zm_ok = cell::zmarch_shape_ok(h->nx, h->ny, h->nz);
+  if (h->zm_ok) {
+    cell::zmarch_prepare();
+    std::vector<float> zb(2048);
+    cell::zmarch_build_b(cell::ZK_UU, h->K0, h->S0, zb.data());
+    cell::zmarch_build_b(cell::ZK_PP4, h->K0, h->S0, zb.data() + 1024);
+    CKS(A.alloc(&h->zb, zb.size()));
+    CK(cudaMemcpy(h->zb, zb.data(), zb.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
   for (int i = 0; i < 1024; ++i) h->kf.K0.k[i] = (float)h->K0[i];
   CKS(A.alloc(&h->K0dev, 1024));
@@ -1248,6 +1267,48 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype) {
     cell::split_f64(static_cast<const double*>(x), h->xh, h->xl, (i64)nrhs * len, h->st);
     cell::resid_df(h->xh, h->xl, len, nullptr, 0, static_cast<double*>(y), len, h->rho32, h->rho_l,
                    h->DF, h->nx, h->ny, h->nz, nrhs, nullptr, h->st);
+  } else {
+    return CELL_EINVAL;
+  }
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
+int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs, int dtype) {
+  if (!h || !x || !y || nrhs < 1 || nrhs > 65535) return CELL_EINVAL;
+  if (block != CELL_BLOCK_A && block != CELL_BLOCK_SBAR) return CELL_EINVAL;
+  const int nc = block == CELL_BLOCK_A ? 3 : 1;
+  const i64 len = nc * h->nn;
+  if (dtype == CELL_F32 || dtype == CELL_F32_TC) {
+    cell::ApplyArgs<float> a{};
+    a.x = static_cast<const float*>(x); a.xs = len; a.y = static_cast<float*>(y); a.ys = len;
+    a.alpha = 1.f; a.rho = h->rho32; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    if (dtype == CELL_F32_TC) {
+      if (!h->zm_ok) return CELL_EINVAL;
+      const int kind = nc == 3 ? cell::ZK_UU : cell::ZK_PP4;
+      cell::apply_zmarch(kind, a, h->zb + 1024 * kind, cell::AM_LINEAR, nrhs, h->tc_err, h->st);
+    } else if (nc == 3) {
+      cell::FixedMat<float, 4> M;
+      for (int i = 0; i < 1024; ++i) M.k[i] = (float)h->K0[i];
+      cell::apply_uu<float>(a, M, cell::AM_LINEAR, nrhs, h->st);
+    } else {
+      cell::FixedMat<float, 1> M;
+      for (int i = 0; i < 64; ++i) M.k[i] = (float)h->S0[i];
+      cell::apply_ss<float>(a, M, cell::AM_LINEAR, nrhs, h->st);
+    }
+  } else if (dtype == CELL_F64) {
+    cell::ApplyArgs<double> a{};
+    a.x = static_cast<const double*>(x); a.xs = len; a.y = static_cast<double*>(y); a.ys = len;
+    a.alpha = 1.0; a.rho = h->rho64; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    if (nc == 3) {
+      cell::FixedMat<double, 4> M;
+      std::memcpy(M.k, h->K0, sizeof(M.k));
+      cell::apply_uu<double>(a, M, cell::AM_LINEAR, nrhs, h->st);
+    } else {
+      cell::FixedMat<double, 1> M;
+      std::memcpy(M.k, h->S0, sizeof(M.k));
+      cell::apply_ss<double>(a, M, cell::AM_LINEAR, nrhs, h->st);
+    }
   } else {
     return CELL_EINVAL;
   }

@@ -135,6 +135,18 @@ void apply_tc_uu(const ApplyArgs<float>& a, const TcTables& T, int mode, int nrh
                  cudaStream_t s);
 void apply_tc_full(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cudaStream_t s);
 
+// Tensor-core fine-level smoother applies marching along z (apply_z.cu,
+// tcgen05 kind::tf32).  ZK_UU: elastic block A (3 -> 3) of one load per CTA;
+// ZK_PP4: local-Schur operator on four loads at once.  B tables (1024 floats
+// per kind) come from zmarch_build_b; zmarch_prepare() once per device before
+// launches or capture.  err counts expired bounded waits.
+enum { ZK_UU = 0, ZK_PP4 = 1 };
+bool zmarch_shape_ok(int nx, int ny, int nz);
+void zmarch_prepare();
+void zmarch_build_b(int kind, const double* K0, const double* S0, float* out);
+void apply_zmarch(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
+                  cudaStream_t s);
+
 // ---- multigrid helpers (mg.cu) ----------------------------------------------
 // r = b, d = c2 Dinv b with c2 read from device memory (*c2p)
 template <typename T, int NC> void cheb_init(const T* b, i64 bs, T* r, i64 rs, T* d, i64 ds,
