@@ -235,7 +235,7 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype);
  * nrhs vectors of [comp][node] (3nn or nn values each), not aliased.
  * dtype CELL_F32 / CELL_F64: SIMT; CELL_F32_TC: the z-marching tensor-core
  * kernel used by the smoothers (TF32 inputs, FP32 accumulation; CELL_EINVAL
- * unless nx % 8 == 0 and nx <= 128).  Asynchronous on the handle's stream. */
+ * unless nx % 8 == 0 and nx <= 64).  Asynchronous on the handle's stream. */
 int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs, int dtype);
 
 /* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as

@@ -307,9 +307,9 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
   if (l == 0) {
     a.rho = K.rho;
     if constexpr (sizeof(T) == 4) {
-      if (h->zm_ok && h->d.opt.tensor_cores >= 1) {
-        const int kind = NC == 3 ? cell::ZK_UU : cell::ZK_PP4;
-        cell::apply_zmarch(kind, a, h->zb + 1024 * kind, mode, 9, h->tc_err, h->st);
+      const int kind = NC == 3 ? cell::ZK_UU : cell::ZK_PP4;
+      if (h->zm_ok && h->d.opt.tensor_cores >= 1 &&
+          cell::apply_zmarch(kind, a, h->zb + 1024 * kind, mode, 9, h->tc_err, h->st)) {
       } else if constexpr (NC == 3) {
         cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
       } else {
@@ -1286,7 +1286,8 @@ int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs
     if (dtype == CELL_F32_TC) {
       if (!h->zm_ok) return CELL_EINVAL;
       const int kind = nc == 3 ? cell::ZK_UU : cell::ZK_PP4;
-      cell::apply_zmarch(kind, a, h->zb + 1024 * kind, cell::AM_LINEAR, nrhs, h->tc_err, h->st);
+      if (!cell::apply_zmarch(kind, a, h->zb + 1024 * kind, cell::AM_LINEAR, nrhs, h->tc_err, h->st))
+        return CELL_EINVAL;
     } else if (nc == 3) {
       cell::FixedMat<float, 4> M;
       for (int i = 0; i < 1024; ++i) M.k[i] = (float)h->K0[i];

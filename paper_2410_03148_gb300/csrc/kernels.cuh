@@ -144,7 +144,8 @@ enum { ZK_UU = 0, ZK_PP4 = 1 };
 bool zmarch_shape_ok(int nx, int ny, int nz);
 void zmarch_prepare();
 void zmarch_build_b(int kind, const double* K0, const double* S0, float* out);
-void apply_zmarch(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
+// Returns false (nothing launched) if a staged array is not 16-byte aligned.
+bool apply_zmarch(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
                   cudaStream_t s);
 
 // ---- multigrid helpers (mg.cu) ----------------------------------------------

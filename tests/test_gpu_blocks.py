@@ -8,9 +8,9 @@ full-operator tests); TF32, component-wise: a TF32 input carries a relative
 error below 2^-10 (truncation of 13 mantissa bits), a TF32-rounded matrix
 entry below 2^-11, so every product term is within 2^-9 of its exact value
 and |y - y_ref| <= 2^-9 (|A| |x|)_i + FP32 accumulation (2e-6 |A||x|).
-Shapes are (nz, ny, nx); the tensor-core kernel needs nx % 8 == 0 and covers
-one tile (nx = 8), several tiles, two TMEM passes (nx = 128), ragged
-15-row y bricks and several z chunks.
+Shapes are (nz, ny, nx); the tensor-core kernel needs nx % 8 == 0 and
+nx <= 64 and is covered with one tile (nx = 8), several tiles, the widest
+row (nx = 64), ragged 15-row y bricks and several z chunks.
 """
 import numpy as np
 import pytest
@@ -61,7 +61,7 @@ def oracle_block(rho, block, x):
     return np.array(ys), np.array(bs), Ke
 
 
-SHAPES = [(3, 4, 8), (5, 17, 16), (7, 31, 24), (40, 16, 32), (4, 8, 128)]
+SHAPES = [(3, 4, 8), (5, 17, 16), (7, 31, 24), (40, 16, 32), (4, 8, 64)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -84,6 +84,15 @@ def test_block_apply_matches_oracle(shape, block, kind):
     else:
         tol = 1e-12 if kind == "f64" else 2e-6
         assert err.max() < tol * np.abs(Ke).max() * np.abs(x).max() * 8
+
+
+@pytest.mark.parametrize("shape", [(4, 4, 72), (4, 4, 12)])
+def test_block_apply_tc_rejects_unsupported_width(shape):
+    from paper_2410_03148_gb300._binding import CellError
+    cell = make_cell(cellgen.random_rho(shape, seed=16))
+    x = torch.zeros((1, 3) + shape, device=dev())
+    with pytest.raises(CellError):
+        cell.apply_block("A", x, tensor_cores=True)
 
 
 @pytest.mark.parametrize("block", ["A", "Sbar"])
