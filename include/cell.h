@@ -189,6 +189,14 @@ int cell_update(cell_handle* h, const void* input);
  * usable best solution) if tol was not reached within max_iter/max_refine. */
 int cell_solve(cell_handle* h, cell_stats* st);
 
+/* cell_solve for n distinct handles (cells of any sizes and options), driven
+ * by up to 16 host threads: handles on different streams solve concurrently
+ * on the GPU, handles sharing a stream one after another.  st: NULL or n
+ * stats (st[i].status holds handle i's result).  Returns CELL_OK, or the
+ * status of the first handle (in list order) that failed; CELL_EINVAL for
+ * a NULL list entry or a handle listed twice (nothing solved). */
+int cell_solve_batch(cell_handle** hs, int n, cell_stats* st);
+
 /* Homogenised tensors of the last solve (Eqs. hom_C, hom_e, hom_kappa with
  * Vol(D) = 1), in SI units, written to host arrays CH[36], eH[18], kH[9].
  * Computed in FP64 in the energy form H_IJ = sum_e rho_e W_e^I.K0 W_e^J

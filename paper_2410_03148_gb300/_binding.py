@@ -24,7 +24,8 @@ CELL_BLOCK_A, CELL_BLOCK_SBAR = 0, 1
 
 # every symbol include/cell.h declares
 EXPORTS = [
-    "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_homogenise", "cell_sensitivity",
+    "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_solve_batch", "cell_homogenise",
+    "cell_sensitivity",
     "cell_dh", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
     "cell_element_matrices", "cell_homogenise_noalloc", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
@@ -90,6 +91,7 @@ def load(path: str = LIB_PATH):
     lib.cell_setup.argtypes = [C.POINTER(cell_desc), C.POINTER(P)]
     lib.cell_update.argtypes = [P, P]
     lib.cell_solve.argtypes = [P, C.POINTER(cell_stats)]
+    lib.cell_solve_batch.argtypes = [C.POINTER(P), C.c_int, C.POINTER(cell_stats)]
     lib.cell_homogenise.argtypes = [P, D, D, D]
     lib.cell_sensitivity.argtypes = [P, D, D, D, P, C.c_int]
     lib.cell_dh.argtypes = [D, D, D, D, D]
@@ -184,6 +186,15 @@ def cell_solve(h, allow_notconv=False):
     s = load().cell_solve(h, C.byref(st))
     _check("cell_solve", s, (CELL_OK, CELL_ENOTCONV) if allow_notconv else (CELL_OK,))
     return s, st
+
+
+def cell_solve_batch(hs, allow_notconv=False):
+    n = len(hs)
+    arr = (C.c_void_p * max(n, 1))(*hs)
+    sts = (cell_stats * max(n, 1))()
+    s = load().cell_solve_batch(arr, n, sts)
+    _check("cell_solve_batch", s, (CELL_OK, CELL_ENOTCONV) if allow_notconv else (CELL_OK,))
+    return s, [sts[i] for i in range(n)]
 
 
 def cell_homogenise(h):

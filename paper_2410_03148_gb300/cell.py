@@ -17,6 +17,32 @@ def _stream_ptr(device):
     return torch.cuda.current_stream(device).cuda_stream
 
 
+def _stats_dict(status, st):
+    return {
+        "status": status,
+        "iters": list(st.iters),
+        "refinements": st.refinements,
+        "rel_residual": list(st.rel_residual),
+        "solve_ms": st.solve_ms,
+        "class_ms": dict(zip(B.PROF_CLASSES, list(st.class_ms))),
+        "class_count": dict(zip(B.PROF_CLASSES, list(st.class_count))),
+        "class_units": dict(zip(B.PROF_CLASSES, list(st.class_units))),
+        "nlevels_u": st.nlevels_u,
+        "nlevels_phi": st.nlevels_phi,
+    }
+
+
+def solve_batch(cells, allow_notconv: bool = False):
+    """Solve several handles at once (cell_solve_batch): cells built on
+    different CUDA streams run concurrently.  Returns the stats of each."""
+    _, sts = B.cell_solve_batch([c._h for c in cells], allow_notconv)
+    out = []
+    for c, st in zip(cells, sts):
+        c.stats = _stats_dict(st.status, st)
+        out.append(c.stats)
+    return out
+
+
 class Cell:
     def __init__(self, design: torch.Tensor, material, kind: str = "phi", rho_void: float = 1e-3,
                  eta: float = 0.0, **options):
@@ -53,18 +79,7 @@ class Cell:
 
     def solve(self, allow_notconv: bool = False):
         status, st = B.cell_solve(self._h, allow_notconv)
-        self.stats = {
-            "status": status,
-            "iters": list(st.iters),
-            "refinements": st.refinements,
-            "rel_residual": list(st.rel_residual),
-            "solve_ms": st.solve_ms,
-            "class_ms": dict(zip(B.PROF_CLASSES, list(st.class_ms))),
-            "class_count": dict(zip(B.PROF_CLASSES, list(st.class_count))),
-            "class_units": dict(zip(B.PROF_CLASSES, list(st.class_units))),
-            "nlevels_u": st.nlevels_u,
-            "nlevels_phi": st.nlevels_phi,
-        }
+        self.stats = _stats_dict(status, st)
         return self.stats
 
     def homogenise(self):

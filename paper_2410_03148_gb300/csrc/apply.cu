@@ -499,7 +499,8 @@ void launch_cslot(const ApplyArgs<float>& a0, int nrhs, cudaStream_t s) {
   constexpr int RG = NCI == 1 ? 3 : 1;
   ApplyArgs<float> a = a0;
   a.nrhs = nrhs;
-  const dim3 g = grid_for(a, (nrhs + RG - 1) / RG);
+  const int groups = (nrhs + RG - 1) / RG;
+  const dim3 g = grid_for(a, groups);
   switch (a.cslot1 - 1) {
     case 0: note_launch(), k_apply_fixed_cslot<0, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
     case 1: note_launch(), k_apply_fixed_cslot<1, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;

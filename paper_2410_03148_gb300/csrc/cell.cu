@@ -7,11 +7,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cell.h"
@@ -221,6 +223,7 @@ struct Krylov {
 
 struct cell_handle {
   cell_desc d{};
+  int dev = 0;             // CUDA device current at set-up
   int nx = 0, ny = 0, nz = 0;
   i64 nn = 0;
   cudaStream_t st = nullptr;
@@ -846,6 +849,7 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   h->nz = d->nz;
   h->nn = (i64)d->nx * d->ny * d->nz;
   h->st = static_cast<cudaStream_t>(d->stream);
+  CK(cudaGetDevice(&h->dev));
   h->prof.on = d->opt.profile != 0;
   h->prof.mask = d->opt.profile_mask ? (unsigned)d->opt.profile_mask : ~0u;
   cellhost::nondimensionalise(d->C, d->e, d->kappa, h->Cn, h->en, h->kn, &h->C0, &h->k0);
@@ -1125,6 +1129,46 @@ int cell_solve(cell_handle* h, cell_stats* st) {
   return solve_impl<double>(h, st);
 }
 
+int cell_solve_batch(cell_handle** hs, int n, cell_stats* st) {
+  if (!hs || n < 0) return CELL_EINVAL;
+  for (int i = 0; i < n; ++i) {
+    if (!hs[i]) return CELL_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return CELL_EINVAL;
+  }
+  // one host worker per handle (at most kBatchThreads): each drives its
+  // handle's solve on the handle's own stream and device, so solves of
+  // handles on different streams overlap on the GPU
+  constexpr int kBatchThreads = 16;
+  std::vector<int> rc(n, CELL_OK);
+  std::vector<std::string> errs(n);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    for (;;) {
+      const int i = next.fetch_add(1);
+      if (i >= n) break;
+      if (cudaSetDevice(hs[i]->dev) != cudaSuccess) {
+        rc[i] = CELL_ECUDA;
+        errs[i] = "cudaSetDevice";
+        continue;
+      }
+      rc[i] = cell_solve(hs[i], st ? st + i : nullptr);
+      if (rc[i] != CELL_OK) errs[i] = g_last_error;
+    }
+  };
+  const int nt = std::min(n, kBatchThreads);
+  std::vector<std::thread> th;
+  th.reserve(nt);
+  for (int t = 0; t < nt; ++t) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  for (int i = 0; i < n; ++i)
+    if (rc[i] != CELL_OK) {
+      g_last_error = errs[i];
+      return rc[i];
+    }
+  return CELL_OK;
+}
+
 int cell_homogenise(cell_handle* h, double CH[36], double eH[18], double kH[9]) {
   if (!h || !CH || !eH || !kH) return CELL_EINVAL;
   if (!h->solved || h->d.opt.load_mask != 0x1FF) return CELL_ESTATE;
@@ -1246,6 +1290,7 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype) {
     cell::ApplyArgs<float> a{};
     a.x = static_cast<const float*>(x); a.xs = len; a.y = static_cast<float*>(y); a.ys = len;
     a.alpha = 1.f; a.rho = h->rho32; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    a.cslot1 = h->cslot1;   // the kernels the solver runs
     cell::FixedMat<float, 4> M;
     for (int i = 0; i < 1024; ++i) M.k[i] = (float)h->K0[i];
     cell::apply_full<float>(a, M, cell::AM_LINEAR, nrhs, h->st);
@@ -1283,6 +1328,7 @@ int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs
     cell::ApplyArgs<float> a{};
     a.x = static_cast<const float*>(x); a.xs = len; a.y = static_cast<float*>(y); a.ys = len;
     a.alpha = 1.f; a.rho = h->rho32; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    a.cslot1 = h->cslot1;   // the kernels the solver runs
     if (dtype == CELL_F32_TC) {
       if (!h->zm_ok) return CELL_EINVAL;
       const int kind = nc == 3 ? cell::ZK_UU : cell::ZK_PP4;

@@ -117,4 +117,14 @@ def test_null_handle_calls_are_rejected(B):
     assert lib.cell_solve(None, None) == B.CELL_EINVAL
     assert lib.cell_homogenise(None, None, None, None) == B.CELL_EINVAL
     assert lib.cell_apply(None, None, None, 1, 0) == B.CELL_EINVAL
+    assert lib.cell_apply_block(None, 0, None, None, 1, 0) == B.CELL_EINVAL
+    # batch: NULL list, negative count, NULL entry, duplicated handle
+    assert lib.cell_solve_batch(None, 1, None) == B.CELL_EINVAL
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert lib.cell_solve_batch(arr, -1, None) == B.CELL_EINVAL
+    assert lib.cell_solve_batch(arr, 2, None) == B.CELL_EINVAL
+    fake = ctypes.c_void_p(16)   # never dereferenced: the duplicate check comes first
+    dup = (ctypes.c_void_p * 2)(fake, fake)
+    assert lib.cell_solve_batch(dup, 2, None) == B.CELL_EINVAL
+    assert lib.cell_solve_batch(arr, 0, None) == B.CELL_OK
     assert B.cell_status_str(B.CELL_ENOTCONV) == "solver did not reach the tolerance"
