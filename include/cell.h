@@ -220,6 +220,24 @@ int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18],
  * singular. */
 int cell_dh(const double C[36], const double e[18], double* dh, double dC[36], double de[18]);
 
+/* Figures of merit of §2.3 on homogenised tensors (SI, Voigt order, host
+ * FP64) and their gradients with respect to every entry of C (dC[36]) and e
+ * (de[18]); dC/de may be NULL, e may be NULL except for CELL_FIG_DH.
+ *   CELL_FIG_DH     d_h = d_zxx + d_zyy + d_zzz, d = e S, S = C^-1 (= cell_dh)
+ *   CELL_FIG_BVOIGT B_Voigt = C_iijj / 9
+ *   CELL_FIG_BREUSS B_Reuss = 1 / S_iijj
+ *   CELL_FIG_CZZZZ  C_zzzz (stiffness along the poling direction, C_33)
+ * The gradients are the upstream dC/de of cell_sensitivity for these
+ * objectives.  CELL_EINVAL for an unknown figure or a singular C. */
+typedef enum cell_figure_kind {
+  CELL_FIG_DH = 0,
+  CELL_FIG_BVOIGT = 1,
+  CELL_FIG_BREUSS = 2,
+  CELL_FIG_CZZZZ = 3
+} cell_figure_kind;
+int cell_figure(int which, const double C[36], const double e[18], double* value, double dC[36],
+                double de[18]);
+
 /* Copy the solutions (total fluctuation fields, loads in order 0..8 whether or
  * not solved) as FP64 cell vectors into the DEVICE buffer out (9*4*N values). */
 int cell_get_solution(cell_handle* h, double* out);

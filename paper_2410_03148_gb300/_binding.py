@@ -26,7 +26,7 @@ CELL_BLOCK_A, CELL_BLOCK_SBAR = 0, 1
 EXPORTS = [
     "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_solve_batch", "cell_homogenise",
     "cell_sensitivity",
-    "cell_dh", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
+    "cell_dh", "cell_figure", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
     "cell_element_matrices", "cell_homogenise_noalloc", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
 ]
@@ -95,6 +95,7 @@ def load(path: str = LIB_PATH):
     lib.cell_homogenise.argtypes = [P, D, D, D]
     lib.cell_sensitivity.argtypes = [P, D, D, D, P, C.c_int]
     lib.cell_dh.argtypes = [D, D, D, D, D]
+    lib.cell_figure.argtypes = [C.c_int, D, D, D, D, D]
     lib.cell_get_solution.argtypes = [P, P]
     lib.cell_apply.argtypes = [P, P, P, C.c_int, C.c_int]
     lib.cell_apply_block.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
@@ -228,6 +229,20 @@ def cell_dh(Cm, em):
     _check("cell_dh", load().cell_dh(Cp, ep, C.byref(dh), dC.ctypes.data_as(C.POINTER(C.c_double)),
                                        de.ctypes.data_as(C.POINTER(C.c_double))))
     return dh.value, dC.reshape(6, 6), de.reshape(3, 6)
+
+
+FIGURES = {"d_h": 0, "B_Voigt": 1, "B_Reuss": 2, "C_zzzz": 3}
+
+
+def cell_figure(which, Cm, em=None):
+    Ca, Cp = _dptr(np.asarray(Cm).reshape(36))
+    ea, ep = _dptr(np.asarray(em if em is not None else np.zeros(18)).reshape(18))
+    v = C.c_double()
+    dC, de = np.zeros(36), np.zeros(18)
+    k = FIGURES[which] if isinstance(which, str) else int(which)
+    _check("cell_figure", load().cell_figure(k, Cp, ep, C.byref(v), dC.ctypes.data_as(C.POINTER(C.c_double)),
+                                               de.ctypes.data_as(C.POINTER(C.c_double))))
+    return v.value, dC.reshape(6, 6), de.reshape(3, 6)
 
 
 def cell_get_solution(h, out_ptr: int):

@@ -144,3 +144,9 @@ class Cell:
 def dh(C, e):
     """d_h and its gradients (host helper of the library)."""
     return B.cell_dh(C, e)
+
+
+def figure(name, C, e=None):
+    """(value, dC, de) of a §2.3 figure of merit: "d_h", "B_Voigt", "B_Reuss"
+    or "C_zzzz" (host helper of the library)."""
+    return B.cell_figure(name, C, e)

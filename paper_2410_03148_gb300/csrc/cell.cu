@@ -1226,55 +1226,101 @@ int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18], c
   return CELL_OK;
 }
 
-int cell_dh(const double C[36], const double e[18], double* dh, double dC[36], double de[18]) {
-  if (!C || !e || !dh) return CELL_EINVAL;
+namespace {
+// 6x6 inverse by Gauss-Jordan with partial pivoting; false if singular.
+bool inverse6(const double* C, double* Inv) {
   double S[36];
   std::memcpy(S, C, sizeof(S));
-  // general 6x6 inverse by Gauss-Jordan with partial pivoting
-  double I6[36] = {0};
-  for (int i = 0; i < 6; ++i) I6[i * 6 + i] = 1.0;
+  for (int i = 0; i < 36; ++i) Inv[i] = 0.0;
+  for (int i = 0; i < 6; ++i) Inv[i * 6 + i] = 1.0;
   for (int k = 0; k < 6; ++k) {
     int p = k;
     for (int i = k + 1; i < 6; ++i)
       if (std::fabs(S[i * 6 + k]) > std::fabs(S[p * 6 + k])) p = i;
-    if (!(std::fabs(S[p * 6 + k]) > 0.0)) return CELL_EINVAL;
+    if (!(std::fabs(S[p * 6 + k]) > 0.0)) return false;
     for (int j = 0; j < 6; ++j) {
       std::swap(S[k * 6 + j], S[p * 6 + j]);
-      std::swap(I6[k * 6 + j], I6[p * 6 + j]);
+      std::swap(Inv[k * 6 + j], Inv[p * 6 + j]);
     }
     const double piv = S[k * 6 + k];
     for (int j = 0; j < 6; ++j) {
       S[k * 6 + j] /= piv;
-      I6[k * 6 + j] /= piv;
+      Inv[k * 6 + j] /= piv;
     }
     for (int i = 0; i < 6; ++i) {
       if (i == k) continue;
       const double f = S[i * 6 + k];
       for (int j = 0; j < 6; ++j) {
         S[i * 6 + j] -= f * S[k * 6 + j];
-        I6[i * 6 + j] -= f * I6[k * 6 + j];
+        Inv[i * 6 + j] -= f * Inv[k * 6 + j];
       }
     }
   }
-  // I6 = C^-1 = S (compliance); d_h = e_3 . S m, m = (1,1,1,0,0,0)
-  double w[6], se3[6];
+  return true;
+}
+}  // namespace
+
+int cell_figure(int which, const double C[36], const double e[18], double* value, double dC[36],
+                double de[18]) {
+  if (!C || !value) return CELL_EINVAL;
+  if (which == CELL_FIG_DH && !e) return CELL_EINVAL;
+  if (which < CELL_FIG_DH || which > CELL_FIG_CZZZZ) return CELL_EINVAL;
+  if (de)
+    for (int i = 0; i < 18; ++i) de[i] = 0.0;
+  if (dC)
+    for (int i = 0; i < 36; ++i) dC[i] = 0.0;
+  if (which == CELL_FIG_BVOIGT) {  // C_iijj / 9: the normal-normal block of Voigt C
+    double v = 0.0;
+    for (int p = 0; p < 3; ++p)
+      for (int q = 0; q < 3; ++q) {
+        v += C[p * 6 + q];
+        if (dC) dC[p * 6 + q] = 1.0 / 9.0;
+      }
+    *value = v / 9.0;
+    return CELL_OK;
+  }
+  if (which == CELL_FIG_CZZZZ) {  // poling-direction stiffness C_33 (Voigt)
+    *value = C[2 * 6 + 2];
+    if (dC) dC[2 * 6 + 2] = 1.0;
+    return CELL_OK;
+  }
+  double S[36];
+  if (!inverse6(C, S)) return CELL_EINVAL;
+  // m = (1,1,1,0,0,0); w = S m, wt = S^T m
+  double w[6], wt[6];
   for (int i = 0; i < 6; ++i) {
-    w[i] = I6[i * 6 + 0] + I6[i * 6 + 1] + I6[i * 6 + 2];
+    w[i] = S[i * 6 + 0] + S[i * 6 + 1] + S[i * 6 + 2];
+    wt[i] = S[0 * 6 + i] + S[1 * 6 + i] + S[2 * 6 + i];
+  }
+  if (which == CELL_FIG_BREUSS) {  // 1 / S_iijj; d(m.S m) = -(S^T m)(S m)^T : dC
+    const double sm = w[0] + w[1] + w[2];
+    if (!(sm != 0.0)) return CELL_EINVAL;
+    *value = 1.0 / sm;
+    if (dC)
+      for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) dC[i * 6 + j] = wt[i] * w[j] / (sm * sm);
+    return CELL_OK;
+  }
+  // d_h = e_3 . S m, d = e S
+  double se3[6];
+  for (int i = 0; i < 6; ++i) {
     double t = 0.0;
-    for (int j = 0; j < 6; ++j) t += I6[i * 6 + j] * e[12 + j];
-    se3[i] = t;
+    for (int j = 0; j < 6; ++j) t += S[j * 6 + i] * e[12 + j];
+    se3[i] = t;   // (S^T e_3)_i
   }
   double v = 0.0;
   for (int p = 0; p < 6; ++p) v += e[12 + p] * w[p];
-  *dh = v;
+  *value = v;
   if (dC)
     for (int i = 0; i < 6; ++i)
       for (int j = 0; j < 6; ++j) dC[i * 6 + j] = -se3[i] * w[j];
-  if (de) {
-    for (int i = 0; i < 18; ++i) de[i] = 0.0;
+  if (de)
     for (int p = 0; p < 6; ++p) de[12 + p] = w[p];
-  }
   return CELL_OK;
+}
+
+int cell_dh(const double C[36], const double e[18], double* dh, double dC[36], double de[18]) {
+  return cell_figure(CELL_FIG_DH, C, e, dh, dC, de);
 }
 
 int cell_get_solution(cell_handle* h, double* out) {

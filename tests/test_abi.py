@@ -84,6 +84,28 @@ def test_dh_helper_matches_oracle(B):
         assert np.abs(de - re_).max() < 1e-12 * np.abs(re_).max()
 
 
+def test_figure_helper_matches_oracle(B):
+    rng = np.random.default_rng(4)
+    for C, e, _ in (cellgen.pzt5a(), cellgen.pzt5h_class()):
+        A = rng.standard_normal((6, 6))
+        C = C + 0.02 * np.abs(C).max() * A   # not symmetric: exercises S^T m in the gradient
+        cases = {"B_Voigt": (figures.b_voigt, figures.b_voigt_grad),
+                 "B_Reuss": (figures.b_reuss, figures.b_reuss_grad),
+                 "C_zzzz": (figures.c_zzzz, figures.c_zzzz_grad)}
+        for name, (f, grad) in cases.items():
+            v, dC, de = B.cell_figure(name, C)
+            assert abs(v - f(C)) < 1e-12 * abs(v)
+            assert np.abs(dC - grad(C)).max() < 1e-12 * np.abs(grad(C)).max()
+            assert not de.any()
+        v, dC, de = B.cell_figure("d_h", C, e)
+        assert abs(v - figures.d_h(C, e)) < 1e-12 * abs(v)
+        rC, re_ = figures.d_h_grad(C, e)
+        assert np.abs(dC - rC).max() < 1e-12 * np.abs(rC).max()
+        assert np.abs(de - re_).max() < 1e-12 * np.abs(re_).max()
+    lib = B.load()
+    assert lib.cell_figure(9, None, None, None, None, None) == B.CELL_EINVAL
+
+
 def test_default_options(B):
     o = B.cell_default_options()
     assert o.tol == 1e-10 and o.restart == 30 and o.load_mask == 0x1FF

@@ -57,6 +57,24 @@ def test_dh_gradient_matches_finite_differences():
         assert abs(fd - de[i, j]) < 1e-8 * abs(f0) + 1e-8
 
 
+def test_dh_gradient_nonsymmetric_C():
+    """Every Voigt entry is an independent variable: the gradient must also
+    hold for a nonsymmetric C (dS = -S dC S gives -(S^T e_3)(S m)^T)."""
+    C = _perturbed_C(11)
+    C[1, 4] += 3e9
+    e = cellgen.pzt5h_class()[1]
+    dC, _ = figures.d_h_grad(C, e)
+    f0 = figures.d_h(C, e)
+    s = 1e-6 * np.abs(C).max()
+    for i in range(6):
+        for j in range(6):
+            Cp, Cm = C.copy(), C.copy()
+            Cp[i, j] += s
+            Cm[i, j] -= s
+            fd = (figures.d_h(Cp, e) - figures.d_h(Cm, e)) / (2 * s)
+            assert abs(fd - dC[i, j]) < 1e-6 * abs(f0) / np.abs(C).max() + 1e-6 * abs(dC[i, j])
+
+
 def test_G_from_si_reproduces_chain_rule():
     """sum G_IJ H_IJ equals sum dC.C^H + de.e^H + dk.kappa^H for a symmetric H."""
     rng = np.random.default_rng(1)
@@ -79,3 +97,36 @@ def test_bulk_moduli_of_isotropic_material():
     C[np.arange(3, 6), np.arange(3, 6)] = mu
     assert abs(figures.b_voigt(C) - (lam + 2 * mu / 3)) < 1e-14
     assert abs(figures.b_reuss(C) - (lam + 2 * mu / 3)) < 1e-13
+
+
+def _perturbed_C(seed):
+    rng = np.random.default_rng(seed)
+    C, _, _ = cellgen.pzt5h_class()
+    A = rng.standard_normal((6, 6))
+    C = C + 0.05 * np.abs(C).max() * (A + A.T) / 6.0
+    assert np.linalg.eigvalsh(C).min() > 0
+    return C
+
+
+def test_reuss_below_voigt():
+    """Hill's bounds: B_Reuss <= B_Voigt for any positive-definite stiffness."""
+    for seed in range(5):
+        C = _perturbed_C(seed)
+        assert figures.b_reuss(C) <= figures.b_voigt(C)
+
+
+def test_bulk_and_czzzz_gradients_match_finite_differences():
+    C = _perturbed_C(7)
+    C[0, 1] += 1e9   # an asymmetric C: every entry is an independent variable
+    for f, grad in ((figures.b_voigt, figures.b_voigt_grad), (figures.b_reuss, figures.b_reuss_grad),
+                    (figures.c_zzzz, figures.c_zzzz_grad)):
+        g = grad(C)
+        f0 = f(C)
+        s = 1e-6 * np.abs(C).max()
+        for i in range(6):
+            for j in range(6):
+                Cp, Cm = C.copy(), C.copy()
+                Cp[i, j] += s
+                Cm[i, j] -= s
+                fd = (f(Cp) - f(Cm)) / (2 * s)
+                assert abs(fd - g[i, j]) < 1e-6 * abs(f0) / np.abs(C).max() + 1e-7 * abs(g[i, j])
