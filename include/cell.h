@@ -115,7 +115,16 @@ typedef struct cell_options {
                           on the caller's stream; the first solve pays the capture */
   int profile_mask;    /* with profile set: bit c (cell_prof_class) = time class c;
                           0 = every class */
+  int precond;         /* CELL_PRECOND_SCP (default, §2.5.3) or CELL_PRECOND_DBP (§2.5.1) */
 } cell_options;
+
+typedef enum cell_precond {
+  CELL_PRECOND_SCP = 0,  /* approximate Schur complement: P = [[A, 0], [-B, Sbar]] */
+  CELL_PRECOND_DBP = 1   /* diagonal blocks: P = diag(A, -C) on the symmetric form, i.e.
+                            diag(A, C) on the nonsymmetric one; the potential block's
+                            multigrid (and cell_apply_block CELL_BLOCK_SBAR) then uses
+                            C = sum_e rho_e C_e */
+} cell_precond;
 
 typedef struct cell_desc {
   int nx, ny, nz;      /* elements (= periodic nodes) per direction, each >= 2 */

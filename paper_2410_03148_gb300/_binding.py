@@ -21,6 +21,7 @@ CELL_FP64, CELL_MIXED_FP32 = 0, 1
 CELL_INPUT_RHO, CELL_INPUT_PHI = 0, 1
 CELL_F32, CELL_F64, CELL_F64_DF, CELL_F32_TC = 0, 1, 2, 3
 CELL_BLOCK_A, CELL_BLOCK_SBAR = 0, 1
+CELL_PRECOND_SCP, CELL_PRECOND_DBP = 0, 1
 
 # every symbol include/cell.h declares
 EXPORTS = [
@@ -40,6 +41,7 @@ class cell_options(C.Structure):
         ("cheb_hi", C.c_double), ("schur_shift", C.c_double), ("coarse_dofs", C.c_int),
         ("load_mask", C.c_int), ("profile", C.c_int), ("tensor_cores", C.c_int),
         ("const_bank", C.c_int), ("graphs", C.c_int), ("profile_mask", C.c_int),
+        ("precond", C.c_int),
     ]
 
 

@@ -579,6 +579,11 @@ void precond(cell_handle* h, const T* v, T* z, const int* mask) {
   Krylov<T>& K = kry<T>(h);
   const i64 nn = h->nn, len = K.len;
   block_solve<T, 3>(h, K.mgu, h->d.opt.vcycles_u, v, len, z, len, K.ru, K.eu, mask);
+  if (h->d.opt.precond == CELL_PRECOND_DBP) {
+    // P_DBP = diag(A, C) in the nonsymmetric form: z_phi ~ C^-1 v_phi
+    block_solve<T, 1>(h, K.mgp, h->d.opt.vcycles_phi, v + 3 * nn, len, z + 3 * nn, len, K.rp, K.ep, mask);
+    return;
+  }
   cell::ApplyArgs<T> a{};
   a.x = z; a.xs = len; a.y = K.tphi; a.ys = nn; a.b = v + 3 * nn; a.bs = len;
   a.alpha = T(1); a.beta = T(1); a.rho = K.rho; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
@@ -795,6 +800,7 @@ int check_options(const cell_options& o) {
   if (!(o.schur_shift >= 0.0) || o.coarse_dofs < 1) return CELL_EINVAL;
   if ((o.load_mask & 0x1FF) == 0 || (o.load_mask & ~0x1FF)) return CELL_EINVAL;
   if (o.tensor_cores < 0 || o.tensor_cores > 2) return CELL_EINVAL;
+  if (o.precond != CELL_PRECOND_SCP && o.precond != CELL_PRECOND_DBP) return CELL_EINVAL;
   return CELL_OK;
 }
 
@@ -860,6 +866,12 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   if (cellhost::local_schur(h->K0, d->opt.schur_shift, h->S0) != 0) {
     set_error("elastic element block is not positive definite (check C)");
     return CELL_EINVAL;
+  }
+  if (d->opt.precond == CELL_PRECOND_DBP) {
+    // diagonal block preconditioner (§2.5.1): the potential block is the
+    // dielectric block C_e itself (K0 = [[A, B^T], [B, -C]]), no coupling
+    for (int a = 0; a < 8; ++a)
+      for (int b = 0; b < 8; ++b) h->S0[a * 8 + b] = -h->K0[(4 * a + 3) * 32 + 4 * b + 3];
   }
   cellhost::affine_loads(h->h, h->Z);
   for (int a = 0; a < 32; ++a)
@@ -1091,6 +1103,7 @@ void cell_default_options(cell_options* o) {
   o->const_bank = 1;
   o->graphs = 1;
   o->profile_mask = 0;
+  o->precond = CELL_PRECOND_SCP;
 }
 
 int cell_setup(const cell_desc* d, cell_handle** out) {
