@@ -223,6 +223,28 @@ int cell_homogenise(cell_handle* h, double CH[36], double eH[18], double kH[9]);
 int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18],
                      const double dk[9], void* g, int dtype);
 
+/* Shape sensitivity on the level set: dL/dphi_n at every node (device
+ * buffer g of nx*ny*nz values, node = i + nx*(j + ny*k), dtype CELL_F32 or
+ * CELL_F64) for the same L as cell_sensitivity.  With the ersatz map of §2.6,
+ * rho_e = 1 - (1 - rho_void) H_eta(phi_e) and phi_e the mean of the element's
+ * 8 nodal values, the chain rule gives dL/dphi_n = sum over the 8 elements
+ * around n of (dL/drho_e) (drho_e/dphi_e) / 8 (element sensitivities in
+ * FP64).  Only for handles set up with CELL_INPUT_PHI (else CELL_EINVAL);
+ * CELL_ESTATE before a successful solve. */
+int cell_sensitivity_phi(cell_handle* h, const double dC[36], const double de[18],
+                         const double dk[9], void* g, int dtype);
+
+/* One explicit time step of the level-set evolution phi_t + v |grad phi| = 0
+ * (Eq. HJ, §2.1) on the periodic nx*ny*nz node grid of the unit cell
+ * (spacing 1/nx, 1/ny, 1/nz): out = phi - dt (max(v,0) |grad phi|+ +
+ * min(v,0) |grad phi|-) with first-order Godunov upwind gradients.  phi, v,
+ * out: device arrays of nx*ny*nz values (node = i + nx*(j + ny*k)), dtype
+ * CELL_F32 or CELL_F64; out must not alias phi.  Stable for
+ * dt max|v| (nx + ny + nz) <= 1.  No handle needed; asynchronous on stream
+ * (NULL = legacy default stream).  CELL_EINVAL for bad sizes or pointers. */
+int cell_hj_step(const void* phi, const void* v, int nx, int ny, int nz, double dt, void* out, int dtype,
+                 void* stream);
+
 /* Hydrostatic strain coefficient d_h = d31 + d32 + d33 with d = e S, S = C^-1
  * (§2.3), and its gradient with respect to every entry of C (dC[36]) and
  * e (de[18]).  Host-only helper; dC/de may be NULL.  CELL_EINVAL if C is

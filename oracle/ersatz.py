@@ -47,3 +47,36 @@ def rho_from_levelset(phi, rho_void=1e-3, eta=None):
     if eta is None:
         eta = 2.0 * max(1.0 / nx, 1.0 / ny, 1.0 / nz)
     return 1.0 - (1.0 - rho_void) * smoothed_heaviside(element_mean(phi), eta)
+
+
+def smoothed_heaviside_deriv(s, eta):
+    """dH_eta/ds = (1 + cos(pi s/eta)) / (2 eta) on |s| <= eta, 0 outside."""
+    s = np.asarray(s, dtype=float)
+    out = np.zeros_like(s)
+    mid = np.abs(s) <= eta
+    out[mid] = 0.5 * (1.0 + np.cos(np.pi * s[mid] / eta)) / eta
+    return out
+
+
+def _eta(phi, eta):
+    nz, ny, nx = phi.shape
+    return 2.0 * max(1.0 / nx, 1.0 / ny, 1.0 / nz) if eta is None else eta
+
+
+def drho_dphi_e(phi, rho_void=1e-3, eta=None):
+    """d rho_e / d phi_e per element (phi_e the element mean)."""
+    return -(1.0 - rho_void) * smoothed_heaviside_deriv(element_mean(phi), _eta(phi, eta))
+
+
+def grad_phi(phi, g_rho, rho_void=1e-3, eta=None):
+    """Nodal dL/dphi from element dL/drho through the ersatz map: every
+    element mean takes 1/8 of each of its 8 nodes, so node n collects
+    g_e drho_e/dphi_e / 8 from the 8 elements that contain it."""
+    ge = np.asarray(g_rho, dtype=float) * drho_dphi_e(phi, rho_void, eta)
+    acc = np.zeros_like(ge)
+    for c in (0, 1):
+        for b in (0, 1):
+            for a in (0, 1):
+                # element (k, j, i) contains node (k + c, j + b, i + a)
+                acc += np.roll(np.roll(np.roll(ge, c, 0), b, 1), a, 2)
+    return acc / 8.0

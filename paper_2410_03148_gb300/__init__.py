@@ -8,11 +8,11 @@ kernels, and importing the binding fails loudly if the library is missing.
 """
 from ._binding import load  # noqa: F401
 
-__all__ = ["load", "Cell", "dh", "figure", "solve_batch", "HomogeniseFn", "homogenise"]
+__all__ = ["load", "Cell", "dh", "figure", "hj_step", "solve_batch", "HomogeniseFn", "homogenise"]
 
 
 def __getattr__(name):
-    if name in ("Cell", "dh", "figure", "solve_batch"):
+    if name in ("Cell", "dh", "figure", "hj_step", "solve_batch"):
         from . import cell
         return getattr(cell, name)
     if name in ("HomogeniseFn", "homogenise"):

@@ -26,7 +26,7 @@ CELL_PRECOND_SCP, CELL_PRECOND_DBP = 0, 1
 # every symbol include/cell.h declares
 EXPORTS = [
     "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_solve_batch", "cell_homogenise",
-    "cell_sensitivity",
+    "cell_sensitivity", "cell_sensitivity_phi", "cell_hj_step",
     "cell_dh", "cell_figure", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
     "cell_element_matrices", "cell_homogenise_noalloc", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
     lib.cell_solve_batch.argtypes = [C.POINTER(P), C.c_int, C.POINTER(cell_stats)]
     lib.cell_homogenise.argtypes = [P, D, D, D]
     lib.cell_sensitivity.argtypes = [P, D, D, D, P, C.c_int]
+    lib.cell_sensitivity_phi.argtypes = [P, D, D, D, P, C.c_int]
+    lib.cell_hj_step.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, C.c_int, P]
     lib.cell_dh.argtypes = [D, D, D, D, D]
     lib.cell_figure.argtypes = [C.c_int, D, D, D, D, D]
     lib.cell_get_solution.argtypes = [P, P]
@@ -210,9 +212,8 @@ def cell_homogenise(h):
     return CH.reshape(6, 6), eH.reshape(3, 6), kH.reshape(3, 3)
 
 
-def cell_sensitivity(h, dC, de, dk, g_ptr: int, dtype: int):
-    keep = []
-    args = []
+def _grad_args(dC, de, dk):
+    keep, args = [], []
     for a, n in ((dC, 36), (de, 18), (dk, 9)):
         if a is None:
             args.append(None)
@@ -220,7 +221,17 @@ def cell_sensitivity(h, dC, de, dk, g_ptr: int, dtype: int):
             arr, p = _dptr(np.asarray(a).reshape(n))
             keep.append(arr)
             args.append(p)
+    return keep, args
+
+
+def cell_sensitivity(h, dC, de, dk, g_ptr: int, dtype: int):
+    keep, args = _grad_args(dC, de, dk)
     _check("cell_sensitivity", load().cell_sensitivity(h, *args, C.c_void_p(g_ptr), dtype))
+
+
+def cell_sensitivity_phi(h, dC, de, dk, g_ptr: int, dtype: int):
+    keep, args = _grad_args(dC, de, dk)
+    _check("cell_sensitivity_phi", load().cell_sensitivity_phi(h, *args, C.c_void_p(g_ptr), dtype))
 
 
 def cell_dh(Cm, em):
@@ -245,6 +256,12 @@ def cell_figure(which, Cm, em=None):
     _check("cell_figure", load().cell_figure(k, Cp, ep, C.byref(v), dC.ctypes.data_as(C.POINTER(C.c_double)),
                                                de.ctypes.data_as(C.POINTER(C.c_double))))
     return v.value, dC.reshape(6, 6), de.reshape(3, 6)
+
+
+def cell_hj_step(phi_ptr: int, v_ptr: int, shape, dt: float, out_ptr: int, dtype: int, stream: int = 0):
+    nz, ny, nx = shape
+    _check("cell_hj_step", load().cell_hj_step(C.c_void_p(phi_ptr), C.c_void_p(v_ptr), nx, ny, nz, dt,
+                                                C.c_void_p(out_ptr), dtype, C.c_void_p(stream)))
 
 
 def cell_get_solution(h, out_ptr: int):

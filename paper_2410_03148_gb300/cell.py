@@ -92,6 +92,13 @@ class Cell:
                            B.CELL_F32 if dtype == torch.float32 else B.CELL_F64)
         return g
 
+    def sensitivity_phi(self, dC=None, de=None, dk=None, dtype=torch.float64) -> torch.Tensor:
+        """dL/dphi at the nodes (shape (nz, ny, nx)) for a level-set handle."""
+        g = torch.empty(self.shape, dtype=dtype, device=self.device)
+        B.cell_sensitivity_phi(self._h, dC, de, dk, g.data_ptr(),
+                               B.CELL_F32 if dtype == torch.float32 else B.CELL_F64)
+        return g
+
     # -- parity / inspection -----------------------------------------------------
     def apply(self, x: torch.Tensor) -> torch.Tensor:
         """y = Ahat x for x of shape (nrhs, 4, nz, ny, nx) (float32 or float64)."""
@@ -144,6 +151,19 @@ class Cell:
 def dh(C, e):
     """d_h and its gradients (host helper of the library)."""
     return B.cell_dh(C, e)
+
+
+def hj_step(phi: torch.Tensor, v: torch.Tensor, dt: float) -> torch.Tensor:
+    """One upwind step of phi_t + v |grad phi| = 0 (Eq. HJ) on the periodic
+    node grid of shape (nz, ny, nx); phi and v CUDA tensors of one dtype."""
+    if not (phi.is_cuda and v.is_cuda) or phi.shape != v.shape or phi.dtype != v.dtype or phi.dim() != 3:
+        raise ValueError("phi and v must be CUDA tensors of one (nz, ny, nx) shape and dtype")
+    phi, v = phi.contiguous(), v.contiguous()
+    out = torch.empty_like(phi)
+    B.cell_hj_step(phi.data_ptr(), v.data_ptr(), tuple(phi.shape), dt, out.data_ptr(),
+                   B.CELL_F32 if phi.dtype == torch.float32 else B.CELL_F64,
+                   torch.cuda.current_stream(phi.device).cuda_stream)
+    return out
 
 
 def figure(name, C, e=None):

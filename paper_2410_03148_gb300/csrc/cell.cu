@@ -234,6 +234,8 @@ struct cell_handle {
   Arena arena;
   float* rho32 = nullptr;
   double* rho64 = nullptr;
+  double* drho = nullptr;   // level-set input: d rho_e / d phi_e (§2.6 smoothing)
+  double* gtmp = nullptr;   // level-set input: element sensitivities before the chain
   double* K0dev = nullptr;
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr;
   // mixed path: x64 as FP32 pairs and rho's low part, for the double-float residual
@@ -814,9 +816,9 @@ int load_design(cell_handle* h, const void* input) {
   if (d->input_kind == CELL_INPUT_PHI) {
     const double eta = d->eta > 0 ? d->eta : 2.0 * std::max(h->h[0], std::max(h->h[1], h->h[2]));
     if (d->input_dtype == CELL_F32)
-      cell::ersatz<float>(static_cast<const float*>(input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
+      cell::ersatz<float>(static_cast<const float*>(input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->drho, h->st);
     else
-      cell::ersatz<double>(static_cast<const double*>(input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->st);
+      cell::ersatz<double>(static_cast<const double*>(input), h->nx, h->ny, h->nz, d->rho_void, eta, h->rho32, h->rho64, h->drho, h->st);
   } else {
     if (d->input_dtype == CELL_F32)
       cell::rho_copy<float>(static_cast<const float*>(input), nn, h->rho32, h->rho64, h->bad, h->st);
@@ -899,6 +901,10 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   Arena& A = h->arena;
   CKS(A.alloc(&h->rho32, nn));
   CKS(A.alloc(&h->rho64, nn));
+  if (d->input_kind == CELL_INPUT_PHI) {
+    CKS(A.alloc(&h->drho, nn));
+    CKS(A.alloc(&h->gtmp, nn));
+  }
   CKS(A.alloc(&h->rho_l, nn));
   CKS(A.alloc(&h->rho_tmp, nn));
   CKS(A.alloc(&h->bad, 1));
@@ -1142,6 +1148,22 @@ int cell_solve(cell_handle* h, cell_stats* st) {
   return solve_impl<double>(h, st);
 }
 
+int cell_hj_step(const void* phi, const void* v, int nx, int ny, int nz, double dt, void* out, int dtype,
+                 void* stream) {
+  if (!phi || !v || !out || nx < 2 || ny < 2 || nz < 2 || !std::isfinite(dt)) return CELL_EINVAL;
+  if (dtype != CELL_F32 && dtype != CELL_F64) return CELL_EINVAL;
+  if (phi == out) return CELL_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (dtype == CELL_F64)
+    cell::hj_step<double>(static_cast<const double*>(phi), static_cast<const double*>(v), nx, ny, nz, dt,
+                          static_cast<double*>(out), s);
+  else
+    cell::hj_step<float>(static_cast<const float*>(phi), static_cast<const float*>(v), nx, ny, nz, dt,
+                         static_cast<float*>(out), s);
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
 int cell_solve_batch(cell_handle** hs, int n, cell_stats* st) {
   if (!hs || n < 0) return CELL_EINVAL;
   for (int i = 0; i < n; ++i) {
@@ -1213,10 +1235,11 @@ int cell_homogenise(cell_handle* h, double CH[36], double eH[18], double kH[9]) 
   return CELL_OK;
 }
 
-int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18], const double dk[9],
-                     void* g, int dtype) {
-  if (!h || !g || (dtype != CELL_F32 && dtype != CELL_F64)) return CELL_EINVAL;
-  if (!h->solved) return CELL_ESTATE;
+namespace {
+// Upstream gradients in SI units -> the nondimensional G of g_e = sum G_IJ
+// W^I.K0 W^J (H = [[C^H, -e^H^T], [-e^H, -kappa^H]] in scaled units).
+cell::SensParams sens_params(const cell_handle* h, const double dC[36], const double de[18],
+                             const double dk[9]) {
   cell::SensParams P;
   std::memcpy(P.Z, h->Z, sizeof(P.Z));
   std::memset(P.G, 0, sizeof(P.G));
@@ -1231,10 +1254,34 @@ int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18], c
     }
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j) P.G[(6 + i) * 9 + 6 + j] = dk ? -h->k0 * dk[i * 3 + j] : 0.0;
+  return P;
+}
+}  // namespace
+
+int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18], const double dk[9],
+                     void* g, int dtype) {
+  if (!h || !g || (dtype != CELL_F32 && dtype != CELL_F64)) return CELL_EINVAL;
+  if (!h->solved) return CELL_ESTATE;
+  const cell::SensParams P = sens_params(h, dC, de, dk);
   if (dtype == CELL_F32)
     cell::sensitivity<float>(h->x64, h->rho64, h->K0dev, P, static_cast<float*>(g), h->nx, h->ny, h->nz, 0, h->st);
   else
     cell::sensitivity<double>(h->x64, h->rho64, h->K0dev, P, static_cast<double*>(g), h->nx, h->ny, h->nz, 0, h->st);
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
+int cell_sensitivity_phi(cell_handle* h, const double dC[36], const double de[18], const double dk[9],
+                         void* g, int dtype) {
+  if (!h || !g || (dtype != CELL_F32 && dtype != CELL_F64)) return CELL_EINVAL;
+  if (h->d.input_kind != CELL_INPUT_PHI || !h->drho) return CELL_EINVAL;
+  if (!h->solved) return CELL_ESTATE;
+  const cell::SensParams P = sens_params(h, dC, de, dk);
+  cell::sensitivity<double>(h->x64, h->rho64, h->K0dev, P, h->gtmp, h->nx, h->ny, h->nz, 0, h->st);
+  if (dtype == CELL_F32)
+    cell::chain_phi<float>(h->gtmp, h->drho, h->nx, h->ny, h->nz, static_cast<float*>(g), h->st);
+  else
+    cell::chain_phi<double>(h->gtmp, h->drho, h->nx, h->ny, h->nz, static_cast<double*>(g), h->st);
   CK(cudaGetLastError());
   return CELL_OK;
 }

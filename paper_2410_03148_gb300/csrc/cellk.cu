@@ -34,7 +34,8 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // rho_e = 1 - (1 - rho_void) H_eta(phi_e), phi_e = mean of the 8 nodal values.
 template <typename Tin>
 __global__ void k_ersatz(const Tin* __restrict__ phi, int nx, int ny, int nz, double rho_void,
-                         double eta, float* __restrict__ r32, double* __restrict__ r64) {
+                         double eta, float* __restrict__ r32, double* __restrict__ r64,
+                         double* __restrict__ drho) {
   const i64 nxy = (i64)nx * ny, nn = nxy * nz;
   const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nn) return;
@@ -46,16 +47,39 @@ __global__ void k_ersatz(const Tin* __restrict__ phi, int nx, int ny, int nz, do
   for (int c = 0; c < 8; ++c)
     s += (double)phi[xs[c & 1] + nx * (ys[(c >> 1) & 1] + (i64)ny * zs[c >> 2])];
   s *= 0.125;
-  double H;
+  double H, dH = 0.0;
   if (s < -eta) H = 0.0;
   else if (s > eta) H = 1.0;
   else {
     const double t = s / eta;
     H = 0.5 * (1.0 + t + sin(M_PI * t) / M_PI);
+    dH = 0.5 * (1.0 + cos(M_PI * t)) / eta;
   }
   const double r = 1.0 - (1.0 - rho_void) * H;
   r64[e] = r;
   r32[e] = (float)r;
+  if (drho) drho[e] = -(1.0 - rho_void) * dH;   // d rho_e / d phi_e
+}
+
+// Nodal level-set sensitivities from element ones: phi_e is the mean of the
+// element's 8 nodal values, so dL/dphi_n = sum over the 8 elements e around
+// n of (dL/drho_e)(drho_e/dphi_e) / 8.
+template <typename T>
+__global__ void k_chain_phi(const double* __restrict__ ge, const double* __restrict__ drho, int nx,
+                            int ny, int nz, T* __restrict__ gn) {
+  const i64 nxy = (i64)nx * ny, nn = nxy * nz;
+  const i64 n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / nxy);
+  const int xs[2] = {i, i == 0 ? nx - 1 : i - 1}, ys[2] = {j, j == 0 ? ny - 1 : j - 1},
+            zs[2] = {k, k == 0 ? nz - 1 : k - 1};
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const i64 e = xs[c & 1] + nx * (ys[(c >> 1) & 1] + (i64)ny * zs[c >> 2]);
+    acc += ge[e] * drho[e];
+  }
+  gn[n] = (T)(0.125 * acc);
 }
 
 template <typename Tin>
@@ -209,11 +233,53 @@ inline unsigned nb(i64 n) { return (unsigned)((n + kB - 1) / kB); }
 
 }  // namespace
 
+// One explicit step of phi_t + v |grad phi| = 0 (Eq. HJ) on the periodic
+// node grid with the first-order Godunov upwind Hamiltonian: one-sided
+// differences D-/D+ per axis, the outward-moving norm built from
+// max(D-, 0) and min(D+, 0), the inward one from min(D-, 0) and max(D+, 0).
+template <typename T>
+__global__ void k_hj_step(const T* __restrict__ phi, const T* __restrict__ v, int nx, int ny, int nz,
+                          double dt, T* __restrict__ out) {
+  const i64 nxy = (i64)nx * ny, nn = nxy * nz;
+  const i64 n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int i = (int)(n % nx), j = (int)((n / nx) % ny), k = (int)(n / nxy);
+  const double p0 = (double)phi[n];
+  const i64 nb[3][2] = {
+      {n - i + (i == 0 ? nx - 1 : i - 1), n - i + (i == nx - 1 ? 0 : i + 1)},
+      {n + ((j == 0 ? ny - 1 : j - 1) - j) * (i64)nx, n + ((j == ny - 1 ? 0 : j + 1) - j) * (i64)nx},
+      {n + ((k == 0 ? nz - 1 : k - 1) - k) * nxy, n + ((k == nz - 1 ? 0 : k + 1) - k) * nxy}};
+  const double hinv[3] = {(double)nx, (double)ny, (double)nz};
+  double gp = 0.0, gm = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double dm = (p0 - (double)phi[nb[d][0]]) * hinv[d];
+    const double dp = ((double)phi[nb[d][1]] - p0) * hinv[d];
+    const double a = fmax(dm, 0.0), b = fmin(dp, 0.0), c = fmin(dm, 0.0), e = fmax(dp, 0.0);
+    gp += a * a + b * b;
+    gm += c * c + e * e;
+  }
+  const double vn = (double)v[n];
+  out[n] = (T)(p0 - dt * (fmax(vn, 0.0) * sqrt(gp) + fmin(vn, 0.0) * sqrt(gm)));
+}
+
 template <typename Tin>
 void ersatz(const Tin* phi, int nx, int ny, int nz, double rho_void, double eta, float* rho32,
-            double* rho64, cudaStream_t s) {
+            double* rho64, double* drho, cudaStream_t s) {
   const i64 nn = (i64)nx * ny * nz;
-  note_launch(), k_ersatz<Tin><<<nb(nn), kB, 0, s>>>(phi, nx, ny, nz, rho_void, eta, rho32, rho64);
+  note_launch(), k_ersatz<Tin><<<nb(nn), kB, 0, s>>>(phi, nx, ny, nz, rho_void, eta, rho32, rho64, drho);
+}
+
+template <typename T>
+void hj_step(const T* phi, const T* v, int nx, int ny, int nz, double dt, T* out, cudaStream_t s) {
+  const i64 nn = (i64)nx * ny * nz;
+  note_launch(), k_hj_step<T><<<nb(nn), kB, 0, s>>>(phi, v, nx, ny, nz, dt, out);
+}
+
+template <typename T>
+void chain_phi(const double* ge, const double* drho, int nx, int ny, int nz, T* gn, cudaStream_t s) {
+  const i64 nn = (i64)nx * ny * nz;
+  note_launch(), k_chain_phi<T><<<nb(nn), kB, 0, s>>>(ge, drho, nx, ny, nz, gn);
 }
 
 template <typename Tin>
@@ -260,8 +326,12 @@ void sensitivity(const double* y, const double* rho, const double* K0dev, const 
                                                                   times_rho);
 }
 
-template void ersatz<float>(const float*, int, int, int, double, double, float*, double*, cudaStream_t);
-template void ersatz<double>(const double*, int, int, int, double, double, float*, double*, cudaStream_t);
+template void ersatz<float>(const float*, int, int, int, double, double, float*, double*, double*, cudaStream_t);
+template void ersatz<double>(const double*, int, int, int, double, double, float*, double*, double*, cudaStream_t);
+template void chain_phi<float>(const double*, const double*, int, int, int, float*, cudaStream_t);
+template void hj_step<float>(const float*, const float*, int, int, int, double, float*, cudaStream_t);
+template void hj_step<double>(const double*, const double*, int, int, int, double, double*, cudaStream_t);
+template void chain_phi<double>(const double*, const double*, int, int, int, double*, cudaStream_t);
 template void rho_copy<float>(const float*, i64, float*, double*, int*, cudaStream_t);
 template void rho_copy<double>(const double*, i64, float*, double*, int*, cudaStream_t);
 template void sensitivity<float>(const double*, const double*, const double*, const SensParams&,

@@ -207,7 +207,14 @@ template <typename T> void fill(T* p, i64 n, T v, cudaStream_t s);
 
 // ---- cell-level kernels (cellk.cu) -------------------------------------------
 template <typename Tin> void ersatz(const Tin* phi, int nx, int ny, int nz, double rho_void,
-                                    double eta, float* rho32, double* rho64, cudaStream_t s);
+                                    double eta, float* rho32, double* rho64, double* drho,
+                                    cudaStream_t s);
+// out = phi - dt v |grad phi| (first-order Godunov upwind, periodic grid)
+template <typename T> void hj_step(const T* phi, const T* v, int nx, int ny, int nz, double dt, T* out,
+                                   cudaStream_t s);
+// gn[node] = sum over the 8 elements around the node of ge[e] drho[e] / 8
+template <typename T> void chain_phi(const double* ge, const double* drho, int nx, int ny, int nz, T* gn,
+                                     cudaStream_t s);
 template <typename Tin> void rho_copy(const Tin* in, i64 n, float* rho32, double* rho64,
                                       int* bad, cudaStream_t s);
 void rhs9(const double* rho, const RhsParams& F, int mask, double* b, int nx, int ny, int nz,

