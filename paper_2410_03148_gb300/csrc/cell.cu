@@ -672,16 +672,17 @@ void iteration(cell_handle* h, int j) {
   precond<T>(h, vj, zj, h->active);
   apply_full_T<T>(h, zj, len, w, len, nullptr, 0, T(1), T(0), h->active, 9);
   // Classical Gram-Schmidt with selective reorthogonalisation: one pass of
-  // dots (w is V_{j+1}, so the same pass also gives |w|^2), one update with
-  // the new norm, and a second pass only for loads whose norm dropped below
-  // 1/sqrt(2) of its value before the pass.
+  // dots (w is V_{j+1}, so the same pass also gives |w|^2); one pass that
+  // updates w and, from the same basis reads, forms the second pass's dots
+  // and the new norm; a second update only for loads whose norm dropped
+  // below 1/sqrt(2) of its value before the first (three basis passes).
   const int ipk = h->prof.begin(s, CELL_PROF_KRYLOV);
   cell::multidot<T>(K.V, vstride, len, j + 2, w, len, len, h->partial, nblk, kNvMax, 9, h->active, s);
   cell::reduce_partials(h->partial, nblk, j + 2, kNvMax, h->hcol, 0, 9, h->active, s);
-  cell::update<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->active, s);
-  cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->active, s);
+  // first update fused with the second pass's dots and the new norm
+  cell::update_dots<T>(K.V, vstride, len, j + 1, h->hcol, kNvMax, w, len, len, h->partial, nblk, 9, h->active, s);
+  cell::reduce_partials(h->partial + (j + 1), nblk, 1, kNvMax, h->hnorm, 0, 9, h->active, s);
   cell::reorth_flag(h->hcol, h->hnorm, j, h->active, h->reorth, 9, s);
-  cell::multidot<T>(K.V, vstride, len, j + 1, w, len, len, h->partial, nblk, kNvMax, 9, h->reorth, s);
   cell::reduce_partials(h->partial, nblk, j + 1, kNvMax, h->ybuf, 0, 9, h->reorth, s);
   cell::update<T>(K.V, vstride, len, j + 1, h->ybuf, kNvMax, w, len, len, 2, h->partial, nblk, 9, h->reorth, s);
   cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->hnorm, 0, 9, h->reorth, s);

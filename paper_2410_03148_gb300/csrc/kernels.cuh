@@ -183,6 +183,11 @@ void reduce_partials(const double* partial, int nblk, int nv, int nvmax, double*
 template <typename T> void update(const T* V, i64 vstride, i64 rstride, int nv, const double* h,
                                   int nvmax, T* w, i64 wstride, i64 len, int mode, double* partial,
                                   int nblk, int nrhs, const int* active, cudaStream_t s);
+// w -= sum_i h[q*nvmax+i] V_i fused with the next pass's partial dots <V_i, w>
+// (partial[..*nvmax + i], i < nv) and |w|^2 (partial[..*nvmax + nv]); nv <= 63
+template <typename T> void update_dots(const T* V, i64 vstride, i64 rstride, int nv, const double* h,
+                                       int nvmax, T* w, i64 wstride, i64 len, double* partial,
+                                       int nblk, int nrhs, const int* active, cudaStream_t s);
 template <typename T> void scale_vec(T* w, i64 wstride, i64 len, const double* sc, int nrhs,
                                      cudaStream_t s);
 template <typename T> void lincomb(const T* V, i64 vstride, i64 rstride, const double* y,

@@ -58,36 +58,84 @@ __device__ __forceinline__ void block_sum_many(double (&v)[G], double (*sh)[G]) 
 
 constexpr int kGrp = 8;
 
-// grid (nblk, nrhs, ceil(nv / kGrp)); each block computes the partial dots of
-// w with the kGrp basis vectors of its group over a contiguous chunk of len.
-template <typename T>
+// grid (nblk, nrhs, ceil(nv / G)); each block computes the partial dots of w
+// with the G basis vectors of its group over a contiguous chunk of len.  The
+// element loop is unrolled so that each thread keeps several elements' loads
+// in flight (these kernels are bound by HBM latency and bandwidth).
+template <typename T, int G>
 __global__ void __launch_bounds__(kB)
 k_multidot(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const T* __restrict__ w,
            i64 wstride, i64 len, double* __restrict__ partial, int nvmax, const int* active) {
-  __shared__ double sh[kWarps][kGrp];
+  __shared__ double sh[kWarps][G];
   const int q = blockIdx.y;
   if (active && !active[q]) return;
-  const int g0 = blockIdx.z * kGrp;
-  const int ng = nv - g0 < kGrp ? nv - g0 : kGrp;
+  const int g0 = blockIdx.z * G;
+  const int ng = nv - g0 < G ? nv - g0 : G;
   const i64 chunk = (len + gridDim.x - 1) / gridDim.x;
   const i64 lo = (i64)blockIdx.x * chunk;
   const i64 hi = lo + chunk < len ? lo + chunk : len;
   const T* W = w + q * wstride;
   const T* V0 = V + q * rstride + (i64)g0 * vstride;
-  T acc[kGrp];
+  T acc[G];
 #pragma unroll
-  for (int i = 0; i < kGrp; ++i) acc[i] = T(0);
+  for (int i = 0; i < G; ++i) acc[i] = T(0);
+#pragma unroll 2
   for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
     const T wk = W[k];
 #pragma unroll
-    for (int i = 0; i < kGrp; ++i)
+    for (int i = 0; i < G; ++i)
       if (i < ng) acc[i] = fma(V0[(i64)i * vstride + k], wk, acc[i]);
   }
-  double d[kGrp];
+  double d[G];
 #pragma unroll
-  for (int i = 0; i < kGrp; ++i) d[i] = (double)acc[i];
-  block_sum_many<kGrp>(d, sh);
+  for (int i = 0; i < G; ++i) d[i] = (double)acc[i];
+  block_sum_many<G>(d, sh);
   if (threadIdx.x < ng) partial[((i64)q * gridDim.x + blockIdx.x) * nvmax + g0 + threadIdx.x] = d[0];
+}
+
+// Fused Gram-Schmidt step: w -= sum_i h_i V_i and, in the same pass, the
+// partial dots <V_i, w_new> (the coefficients of the next classical pass)
+// and |w_new|^2 -> partial[..*nvmax + i] (i < nv) and [..*nvmax + nv].  Each
+// thread keeps the nv basis values of its element in registers, so the basis
+// is read once for both.  nv <= G.
+template <typename T, int G>
+__global__ void __launch_bounds__(kB)
+k_update_dots(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const double* __restrict__ h,
+              int nvmax, T* __restrict__ w, i64 wstride, i64 len, double* __restrict__ partial,
+              const int* active) {
+  __shared__ double sh[kWarps][G + 1];
+  __shared__ T hs[G];
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  for (int i = threadIdx.x; i < G; i += kB) hs[i] = i < nv ? (T)h[q * nvmax + i] : T(0);
+  __syncthreads();
+  const i64 chunk = (len + gridDim.x - 1) / gridDim.x;
+  const i64 lo = (i64)blockIdx.x * chunk;
+  const i64 hi = lo + chunk < len ? lo + chunk : len;
+  T* W = w + q * wstride;
+  const T* V0 = V + q * rstride;
+  T acc[G + 1];
+#pragma unroll
+  for (int i = 0; i <= G; ++i) acc[i] = T(0);
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
+    T v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) v[i] = i < nv ? V0[(i64)i * vstride + k] : T(0);
+    T x = W[k];
+#pragma unroll
+    for (int i = 0; i < G; ++i) x = fma(-hs[i], v[i], x);
+    W[k] = x;
+#pragma unroll
+    for (int i = 0; i < G; ++i) acc[i] = fma(v[i], x, acc[i]);
+    acc[G] = fma(x, x, acc[G]);
+  }
+  double d[G + 1];
+#pragma unroll
+  for (int i = 0; i <= G; ++i) d[i] = (double)acc[i];
+  block_sum_many<G + 1>(d, sh);
+  const i64 base = ((i64)q * gridDim.x + blockIdx.x) * nvmax;
+  if (threadIdx.x < nv) partial[base + threadIdx.x] = d[0];
+  if (threadIdx.x == G) partial[base + nv] = d[0];
 }
 
 // One warp per (rhs, i): fixed-order sum over blocks.
@@ -122,6 +170,7 @@ k_update(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const double
   T* W = w + q * wstride;
   const T* V0 = V + q * rstride;
   T nrm = T(0);
+#pragma unroll 2
   for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
     T x = W[k];
     const T* vp = V0 + k;
@@ -167,10 +216,12 @@ __global__ void k_lincomb(const T* __restrict__ V, i64 vstride, i64 rstride,
   __syncthreads();
   const T* V0 = V + q * rstride;
   T* U = u + q * ustride;
+  // accumulate in the vector type: the basis is T already, and FP64
+  // arithmetic (1/64 rate) would dominate this pass for FP32 vectors
   for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int i = 0; i < kq; ++i) acc += ys[i] * (double)V0[i * vstride + k];
-    U[k] = (T)acc;
+    T acc = T(0);
+    for (int i = 0; i < kq; ++i) acc = fma((T)ys[i], V0[i * vstride + k], acc);
+    U[k] = acc;
   }
 }
 
@@ -301,9 +352,26 @@ inline unsigned stream_blocks(i64 len) {
 template <typename T>
 void multidot(const T* V, i64 vstride, i64 rstride, int nv, const T* w, i64 wstride, i64 len,
               double* partial, int nblk, int nvmax, int nrhs, const int* active, cudaStream_t s) {
+  // one group of up to 16 vectors per block (w read once), else groups of 8
+  if (nv <= 16) {
+    note_launch(), k_multidot<T, 16><<<dim3(nblk, nrhs, 1), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride,
+                                                                        len, partial, nvmax, active);
+    return;
+  }
   const unsigned ng = (unsigned)((nv + kGrp - 1) / kGrp);
-  note_launch(), k_multidot<T><<<dim3(nblk, nrhs, ng), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride,
-                                                                   len, partial, nvmax, active);
+  note_launch(), k_multidot<T, kGrp><<<dim3(nblk, nrhs, ng), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride,
+                                                                         len, partial, nvmax, active);
+}
+
+template <typename T>
+void update_dots(const T* V, i64 vstride, i64 rstride, int nv, const double* h, int nvmax, T* w,
+                 i64 wstride, i64 len, double* partial, int nblk, int nrhs, const int* active,
+                 cudaStream_t s) {
+  const dim3 g(nblk, nrhs);
+  if (nv <= 8) note_launch(), k_update_dots<T, 8><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
+  else if (nv <= 16) note_launch(), k_update_dots<T, 16><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
+  else if (nv <= 32) note_launch(), k_update_dots<T, 32><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
+  else note_launch(), k_update_dots<T, 63><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
 }
 
 void reduce_partials(const double* partial, int nblk, int nv, int nvmax, double* out, int accumulate,
@@ -378,6 +446,8 @@ void fill(T* p, i64 n, T v, cudaStream_t s) {
                             const int*, cudaStream_t);                                             \
   template void update<T>(const T*, i64, i64, int, const double*, int, T*, i64, i64, int, double*, \
                           int, int, const int*, cudaStream_t);                                     \
+  template void update_dots<T>(const T*, i64, i64, int, const double*, int, T*, i64, i64, double*, \
+                               int, int, const int*, cudaStream_t);                                \
   template void scale_vec<T>(T*, i64, i64, const double*, int, cudaStream_t);                      \
   template void lincomb<T>(const T*, i64, i64, const double*, const int*, int, T*, i64, i64, int,  \
                            const int*, cudaStream_t);                                              \
