@@ -22,6 +22,7 @@ namespace cell {
 namespace {
 
 constexpr int kBlock = 128;
+constexpr long long kSplitMaxNodes = 4096;   // levels up to 16^3 use the four-lane stencil apply
 
 struct NodeIdx {
   i64 xo[3], yo[3], zo[3];
@@ -370,6 +371,74 @@ __global__ void __launch_bounds__(kBlock) k_apply_st(const ApplyArgs<T> a, int n
   }
 }
 
+// Small coarse levels are bound by the latency of the 27 dependent neighbour
+// rounds of k_apply_st, not by throughput: here four lanes share one (node,
+// load), each taking the neighbours q = lane, lane + 4, ... (7 or 6 of the
+// 27), and the partial sums meet by two butterfly shuffles.  Lane 0 of each
+// group runs the epilogue.  Grid (ceil(4 nx ny / kBlock), nz, nrhs).
+template <typename T, int NC, int MODE>
+__global__ void __launch_bounds__(kBlock) k_apply_st_split(const ApplyArgs<T> a, int nrhs) {
+  const int r = blockIdx.z;
+  if (r >= nrhs || (a.active && !a.active[r])) return;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane4 = g & 3;
+  const int p = g >> 2;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const bool valid = p < nx * ny;   // whole groups of 4 share p: shuffles stay full-warp
+  NodeIdx t;
+  T acc[NC], dold[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = dold[c] = T(0);
+  if (valid) {
+    const int j = p / nx, i = p - j * nx, k = blockIdx.y;
+    const i64 nxy = (i64)nx * ny;
+    t.nn = nxy * nz;
+    t.n = (i64)k * nxy + p;
+    t.xo[0] = i == 0 ? nx - 1 : i - 1;
+    t.xo[1] = i;
+    t.xo[2] = i == nx - 1 ? 0 : i + 1;
+    t.yo[0] = (i64)(j == 0 ? ny - 1 : j - 1) * nx;
+    t.yo[1] = (i64)j * nx;
+    t.yo[2] = (i64)(j == ny - 1 ? 0 : j + 1) * nx;
+    t.zo[0] = (i64)(k == 0 ? nz - 1 : k - 1) * nxy;
+    t.zo[1] = (i64)k * nxy;
+    t.zo[2] = (i64)(k == nz - 1 ? 0 : k + 1) * nxy;
+    const T* X = a.x + r * a.xs;
+    const T* S = a.st + t.n;
+#pragma unroll
+    for (int kk = 0; kk < 7; ++kk) {
+      const int q = 4 * kk + lane4;
+      if (q < 27) {
+        const int qx = q % 3, qy = (q / 3) % 3, qz = q / 9;
+        const i64 ox = qx == 0 ? t.xo[0] : (qx == 1 ? t.xo[1] : t.xo[2]);
+        const i64 oy = qy == 0 ? t.yo[0] : (qy == 1 ? t.yo[1] : t.yo[2]);
+        const i64 oz = qz == 0 ? t.zo[0] : (qz == 1 ? t.zo[1] : t.zo[2]);
+        const i64 m = ox + oy + oz;
+        T xv[NC];
+#pragma unroll
+        for (int d = 0; d < NC; ++d) xv[d] = __ldg(X + d * t.nn + m);
+        if (q == 13) {
+#pragma unroll
+          for (int d = 0; d < NC; ++d) dold[d] = xv[d];
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int d = 0; d < NC; ++d)
+            acc[c] = fma(__ldg(S + (i64)((q * NC + c) * NC + d) * t.nn), xv[d], acc[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 1);
+    acc[c] += __shfl_xor_sync(0xffffffffu, acc[c], 2);
+    dold[c] = __shfl_sync(0xffffffffu, dold[c], (threadIdx.x & ~3) | 1);   // q = 13 is lane 1
+  }
+  if (!valid || lane4 != 0) return;
+  epilogue<T, NC, MODE>(a, r, t, acc, dold);
+}
+
 // One thread per (node, output component c): accumulate the element blocks of
 // the 8 elements around the node into its 27 neighbour blocks.
 template <typename T, int NC>
@@ -588,10 +657,22 @@ void launch_st(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
 }
 
 template <typename T, int NC>
+void launch_st_split(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
+  const dim3 g((unsigned)((4 * a.nx * a.ny + kBlock - 1) / kBlock), (unsigned)a.nz, (unsigned)nrhs);
+  switch (mode) {
+    case AM_LINEAR: note_launch(), k_apply_st_split<T, NC, AM_LINEAR><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    case AM_CHEB: note_launch(), k_apply_st_split<T, NC, AM_CHEB><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    case AM_CHEB_LAST: note_launch(), k_apply_st_split<T, NC, AM_CHEB_LAST><<<g, kBlock, 0, s>>>(a, nrhs); break;
+    default: note_launch(), k_apply_st_split<T, NC, AM_RESID_CHEB0><<<g, kBlock, 0, s>>>(a, nrhs); break;
+  }
+}
+
+template <typename T, int NC>
 void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
   const long long nn = (long long)a.nx * a.ny * a.nz;
   if (nn > 65536) launch_st<T, NC, 3>(a, mode, nrhs, s);
-  else launch_st<T, NC, 1>(a, mode, nrhs, s);
+  else if (nn > kSplitMaxNodes) launch_st<T, NC, 1>(a, mode, nrhs, s);
+  else launch_st_split<T, NC>(a, mode, nrhs, s);
 }
 
 template <typename T, int NC>
