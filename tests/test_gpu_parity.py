@@ -475,3 +475,40 @@ def test_hj_step_matches_oracle(dtype):
     ref = levelset.hj_step(pt.double().cpu().numpy(), vt.double().cpu().numpy(), dt)
     tol = 1e-14 if dtype == torch.float64 else 1e-6
     assert np.abs(out - ref).max() < tol * np.abs(ref).max()
+
+
+def test_dh_gradient_matches_central_differences_64cube():
+    """Differentiation at the 64^3 size: d(d_h)/d(rho_e) from the sensitivity
+    kernel against central differences of the library's own solves at 16
+    seeded elements (8 on the interface, 0.01 < rho < 0.99, and 8 solid).
+    Step 1e-3 on rho_e: H is smooth in rho, so the truncation error is
+    O(step^2); a smaller step would drown in the rounding of the 262,144-term
+    energy sums (~1e-14 relative)."""
+    from paper_2410_03148_gb300 import dh
+    shape = (64, 64, 64)
+    phi = cellgen.gaussian_levelset(shape, seed=0)
+    opts = dict(precision=1)   # tol 1e-10: the energy-form H is then exact to ~1e-20
+    base = make_cell(phi, "phi", **opts)
+    base.solve()
+    Ch, eh, _ = base.homogenise()
+    d0, dC, de = dh(Ch, eh)
+    g = base.sensitivity(dC, de, None).cpu().numpy().ravel()
+    rho = base.rho().cpu().numpy()
+    r = rho.ravel()
+    rng = np.random.default_rng(1234)
+    inter = np.flatnonzero((r > 0.01) & (r < 0.99))
+    solid = np.flatnonzero(r > 0.999)
+    picks = list(rng.choice(inter, 8, replace=False)) + list(rng.choice(solid, 8, replace=False))
+    cell = make_cell(rho, "rho", **opts)
+    step = 1e-3
+    for e in picks:
+        vals = []
+        for sgn in (1, -1):
+            rp = r.copy()
+            rp[e] += sgn * step
+            cell.update(torch.as_tensor(rp.reshape(shape), device=dev()))
+            cell.solve()
+            C2, e2, _ = cell.homogenise()
+            vals.append(dh(C2, e2)[0])
+        fd = (vals[0] - vals[1]) / (2 * step)
+        assert abs(fd - g[e]) < 1e-5 * abs(g[e]) + 1e-6 * np.abs(g).max(), (e, fd, g[e])
