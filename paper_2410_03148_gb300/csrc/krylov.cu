@@ -181,6 +181,57 @@ k_update4(const float* __restrict__ V, i64 vstride, i64 rstride, int nv, const d
   }
 }
 
+// k_update_dots with 16-byte loads (FP32, nv <= G <= 16: the nv basis
+// float4 values of the element stay in registers between the update and the
+// dots).
+template <int G>
+__global__ void __launch_bounds__(kB)
+k_update_dots4(const float* __restrict__ V, i64 vstride, i64 rstride, int nv, const double* __restrict__ h,
+               int nvmax, float* __restrict__ w, i64 wstride, i64 len, double* __restrict__ partial,
+               const int* active) {
+  __shared__ double sh[kWarps][G + 1];
+  __shared__ float hs[G];
+  const int q = blockIdx.y;
+  if (active && !active[q]) return;
+  for (int i = threadIdx.x; i < G; i += kB) hs[i] = i < nv ? (float)h[q * nvmax + i] : 0.f;
+  __syncthreads();
+  const i64 len4 = len >> 2;
+  const i64 chunk = (len4 + gridDim.x - 1) / gridDim.x;
+  const i64 lo = (i64)blockIdx.x * chunk;
+  const i64 hi = lo + chunk < len4 ? lo + chunk : len4;
+  float4* W = reinterpret_cast<float4*>(w + q * wstride);
+  const float* V0 = V + q * rstride;
+  float acc[G + 1];
+#pragma unroll
+  for (int i = 0; i <= G; ++i) acc[i] = 0.f;
+  for (i64 k = lo + threadIdx.x; k < hi; k += kB) {
+    float4 v[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i)
+      v[i] = i < nv ? reinterpret_cast<const float4*>(V0 + (i64)i * vstride)[k] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 x = W[k];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+      const float hi_ = -hs[i];
+      x.x = fmaf(hi_, v[i].x, x.x);
+      x.y = fmaf(hi_, v[i].y, x.y);
+      x.z = fmaf(hi_, v[i].z, x.z);
+      x.w = fmaf(hi_, v[i].w, x.w);
+    }
+    W[k] = x;
+#pragma unroll
+    for (int i = 0; i < G; ++i) acc[i] = dot4(v[i], x, acc[i]);
+    acc[G] = dot4(x, x, acc[G]);
+  }
+  double d[G + 1];
+#pragma unroll
+  for (int i = 0; i <= G; ++i) d[i] = (double)acc[i];
+  block_sum_many<G + 1>(d, sh);
+  const i64 base = ((i64)q * gridDim.x + blockIdx.x) * nvmax;
+  if (threadIdx.x < nv) partial[base + threadIdx.x] = d[0];
+  if (threadIdx.x == G) partial[base + nv] = d[0];
+}
+
 inline bool vec4_ok(const void* a, const void* b, i64 s1, i64 s2, i64 len) {
   return ((uintptr_t)a & 15u) == 0 && ((uintptr_t)b & 15u) == 0 && s1 % 4 == 0 && s2 % 4 == 0 && len % 4 == 0;
 }
@@ -468,6 +519,13 @@ void update_dots(const T* V, i64 vstride, i64 rstride, int nv, const double* h, 
                  i64 wstride, i64 len, double* partial, int nblk, int nrhs, const int* active,
                  cudaStream_t s) {
   const dim3 g(nblk, nrhs);
+  if constexpr (sizeof(T) == 4) {
+    if (nv <= 16 && vec4_ok(V, w, vstride, rstride, len) && wstride % 4 == 0) {
+      if (nv <= 8) note_launch(), k_update_dots4<8><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
+      else note_launch(), k_update_dots4<16><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
+      return;
+    }
+  }
   if (nv <= 8) note_launch(), k_update_dots<T, 8><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
   else if (nv <= 16) note_launch(), k_update_dots<T, 16><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
   else if (nv <= 32) note_launch(), k_update_dots<T, 32><<<g, kB, 0, s>>>(V, vstride, rstride, nv, h, nvmax, w, wstride, len, partial, active);
