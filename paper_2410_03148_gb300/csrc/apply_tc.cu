@@ -9,7 +9,8 @@
 // split x = xh + xl, K = Kh + Kl (each TF32) the products xh Kh + xh Kl + xl Kh
 // recover FP32 accuracy ("3xTF32").
 //
-// One CTA (128 threads) owns a brick of 16 x 4 x 2 nodes and a group of
+// Used for the full operator Ahat (NC = 4, potential rows negated).  One CTA
+// (128 threads) owns a brick of 16 x 4 x 2 nodes and a group of
 // loads.  Per load it stages the x values of the 18 x 6 x 4 halo nodes in
 // shared memory and builds the gathered rows of the 17 x 5 x 3 = 255 elements
 // touching the brick as a K-major no-swizzle operand (two M = 128 tiles).
@@ -260,8 +261,8 @@ void launch(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cu
   using P = Plan<NC>;
   const int rg = 3;
   const dim3 g((unsigned)((a.nx / BX) * (a.ny / BY)), (unsigned)(a.nz / BZ), (unsigned)((nrhs + rg - 1) / rg));
-  const float* Bt = NC == 3 ? T.b_uu : T.b_full;
-  const unsigned short* gs = NC == 3 ? T.g_uu : T.g_full;
+  const float* Bt = T.b_full;
+  const unsigned short* gs = T.g_full;
   note_launch(), k_apply_tc<NC, MODE, NEG><<<g, kThreads, P::SMEM, s>>>(a, Bt, gs, nrhs, rg, err);
 }
 
@@ -311,35 +312,17 @@ void build_tables(const double* K0, float* btiles, unsigned short* gsrc) {
 
 // Opt the kernels into their dynamic shared memory (once per device, before
 // any launch or graph capture).
-void tc_prepare() {
-  set_smem_attr<3, AM_LINEAR, false>();
-  set_smem_attr<3, AM_CHEB, false>();
-  set_smem_attr<3, AM_CHEB_LAST, false>();
-  set_smem_attr<3, AM_RESID_CHEB0, false>();
-  set_smem_attr<4, AM_LINEAR, true>();
-}
+void tc_prepare() { set_smem_attr<4, AM_LINEAR, true>(); }
 
 bool tc_shape_ok(int nx, int ny, int nz) {
   return nx % BX == 0 && ny % BY == 0 && nz % BZ == 0 && nx >= BX && ny >= BY && nz >= BZ;
 }
 
-size_t tc_table_floats(int nc) { return nc == 3 ? 2 * Plan<3>::BBYTES / 4 : 2 * Plan<4>::BBYTES / 4; }
-size_t tc_table_idx(int nc) { return nc == 3 ? Plan<3>::CM * 32 : Plan<4>::CM * 32; }
+size_t tc_table_floats() { return 2 * Plan<4>::BBYTES / 4; }
+size_t tc_table_idx() { return Plan<4>::CM * 32; }
 
-void tc_build_tables_host(const double* K0, float* b_uu, unsigned short* g_uu, float* b_full,
-                          unsigned short* g_full) {
-  build_tables<3>(K0, b_uu, g_uu);
+void tc_build_tables_host(const double* K0, float* b_full, unsigned short* g_full) {
   build_tables<4>(K0, b_full, g_full);
-}
-
-void apply_tc_uu(const ApplyArgs<float>& a, const TcTables& T, int mode, int nrhs, int* err,
-                 cudaStream_t s) {
-  switch (mode) {
-    case AM_LINEAR: launch<3, AM_LINEAR, false>(a, T, nrhs, err, s); break;
-    case AM_CHEB: launch<3, AM_CHEB, false>(a, T, nrhs, err, s); break;
-    case AM_CHEB_LAST: launch<3, AM_CHEB_LAST, false>(a, T, nrhs, err, s); break;
-    default: launch<3, AM_RESID_CHEB0, false>(a, T, nrhs, err, s); break;
-  }
 }
 
 void apply_tc_full(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cudaStream_t s) {

@@ -914,22 +914,16 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   h->tc_ok = cell::tc_shape_ok(h->nx, h->ny, h->nz);
   if (h->tc_ok) {
     cell::tc_prepare();
-    std::vector<float> bu(cell::tc_table_floats(3)), bf(cell::tc_table_floats(4));
-    std::vector<unsigned short> gu(cell::tc_table_idx(3)), gf(cell::tc_table_idx(4));
-    cell::tc_build_tables_host(h->K0, bu.data(), gu.data(), bf.data(), gf.data());
-    float *dbu, *dbf;
-    unsigned short *dgu, *dgf;
-    CKS(A.alloc(&dbu, bu.size()));
+    std::vector<float> bf(cell::tc_table_floats());
+    std::vector<unsigned short> gf(cell::tc_table_idx());
+    cell::tc_build_tables_host(h->K0, bf.data(), gf.data());
+    float* dbf;
+    unsigned short* dgf;
     CKS(A.alloc(&dbf, bf.size()));
-    CKS(A.alloc(&dgu, gu.size()));
     CKS(A.alloc(&dgf, gf.size()));
-    CK(cudaMemcpy(dbu, bu.data(), bu.size() * sizeof(float), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dbf, bf.data(), bf.size() * sizeof(float), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(dgu, gu.data(), gu.size() * 2, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(dgf, gf.data(), gf.size() * 2, cudaMemcpyHostToDevice));
-    h->tct.b_uu = dbu;
     h->tct.b_full = dbf;
-    h->tct.g_uu = dgu;
     h->tct.g_full = dgf;
   }
   h->zm_ok = cell::zmarch_shape_ok(h->nx, h->ny, h->nz);

@@ -115,24 +115,19 @@ template <typename T> void axpy_split(double* x, float* xh, float* xl, i64 xs, c
                                       i64 len, const double* sc, int nrhs, const int* active,
                                       cudaStream_t s);
 
-// Tensor-core (tcgen05, 3xTF32) element applies (apply_tc.cu); the grid must
-// satisfy tc_shape_ok.  err counts bounded-wait expiries.  The tables (element
-// block in the operand layout, hi and lo TF32 parts; gather indices) are built
-// on the host once per material and grid.
+// Tensor-core (tcgen05, 3xTF32) full-operator apply (apply_tc.cu); the grid
+// must satisfy tc_shape_ok.  err counts bounded-wait expiries.  The tables
+// (element matrix in the operand layout, hi and lo TF32 parts; gather
+// indices) are built on the host once per material and grid.
 struct TcTables {
-  const float* b_uu = nullptr;
-  const unsigned short* g_uu = nullptr;
   const float* b_full = nullptr;
   const unsigned short* g_full = nullptr;
 };
 bool tc_shape_ok(int nx, int ny, int nz);
 void tc_prepare();
-size_t tc_table_floats(int nc);
-size_t tc_table_idx(int nc);
-void tc_build_tables_host(const double* K0, float* b_uu, unsigned short* g_uu, float* b_full,
-                          unsigned short* g_full);
-void apply_tc_uu(const ApplyArgs<float>& a, const TcTables& T, int mode, int nrhs, int* err,
-                 cudaStream_t s);
+size_t tc_table_floats();
+size_t tc_table_idx();
+void tc_build_tables_host(const double* K0, float* b_full, unsigned short* g_full);
 void apply_tc_full(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cudaStream_t s);
 
 // Tensor-core fine-level smoother applies marching along z (apply_z.cu,
