@@ -69,6 +69,24 @@ def parse():
     return ap.parse_args()
 
 
+def rank_seeds(rank, ndes):
+    """Design seeds of one rank: disjoint across ranks (replicas solve
+    independent designs, no data-path collective)."""
+    return [rank * 1000 + s for s in range(ndes)]
+
+
+def job_ms_per_cell(total_ms, steps, world, dist=None):
+    """Whole-job figure from one rank's timed region: the slowest rank's time
+    (max over ranks) for all steps x world cells."""
+    if world > 1 and dist is not None:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64,
+                         device="cuda" if dist.get_backend() == "nccl" else "cpu")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return total_ms, total_ms / (steps * world)
+
+
 def traffic_table():
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -219,8 +237,8 @@ def main():
     n = args.n
     prec = 1 if args.precision == "mixed" else 0
     ndes = 8
-    designs = [torch.as_tensor(cellgen.gaussian_levelset(n, seed=rank * 1000 + s), device=dev)
-               for s in range(ndes)]
+    designs = [torch.as_tensor(cellgen.gaussian_levelset(n, seed=sd), device=dev)
+               for sd in rank_seeds(rank, ndes)]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
     # One handle per process (all device memory allocated here, once); every
@@ -279,12 +297,7 @@ def main():
     wall = time.perf_counter() - t_start
     launches = B.cell_launch_count() - launches0
     clocks = sampler.stop()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_cell = total_ms / (args.steps * world)
+    total_ms, ms_per_cell = job_ms_per_cell(sum(step_ms), args.steps, world, dist if world > 1 else None)
 
     # roofline of the dominant kernel class, from the live CUDA events
     hbm, hbm_kind, sm_max = peaks()
