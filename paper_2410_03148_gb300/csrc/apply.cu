@@ -670,7 +670,7 @@ void launch_st_split(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) 
 template <typename T, int NC>
 void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
   const long long nn = (long long)a.nx * a.ny * a.nz;
-  if (nn > 65536) launch_st<T, NC, 3>(a, mode, nrhs, s);
+  if (nn > 16384) launch_st<T, NC, 3>(a, mode, nrhs, s);
   else if (nn > kSplitMaxNodes) launch_st<T, NC, 1>(a, mode, nrhs, s);
   else launch_st_split<T, NC>(a, mode, nrhs, s);
 }
