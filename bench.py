@@ -30,6 +30,12 @@ import sys
 import tempfile
 import time
 
+# The CPU oracle (reference arm and cpu_baseline) is timed on one host core:
+# pin the BLAS thread pools before numpy is first imported, so that the
+# reported core count is the one used.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
