@@ -194,6 +194,7 @@ struct BlockMG {
   int nc = 0;
   std::vector<Level<T>> lv;
   T* fixedm = nullptr;   // device copy of the level-0 element block ((8nc)^2)
+  T* childm = nullptr;   // the 8 child matrices P_c^T K P_c of level 1 (8 (8nc)^2)
   std::vector<double> fixed_host;
   std::vector<T> dense_host;   // staging of the coarsest inverse (kept alive for the async copy)
   std::vector<T> cc_host;      // staging of the Chebyshev coefficients of all levels
@@ -378,6 +379,28 @@ int alloc_mg(cell_handle* h, BlockMG<T>& mg, const double* fixed_block) {
   for (int i = 0; i < R * R; ++i) fb[i] = (T)fixed_block[i];
   CKS(h->arena.alloc(&mg.fixedm, R * R));
   CK(cudaMemcpyAsync(mg.fixedm, fb.data(), R * R * sizeof(T), cudaMemcpyHostToDevice, h->st));
+  // G_c[(A, d), (B, e)] = sum_{a, b} w(c, a, A) w(c, b, B) K[(a, d), (b, e)]
+  {
+    std::vector<T> G((size_t)8 * R * R);
+    for (int c = 0; c < 8; ++c)
+      for (int A = 0; A < 8; ++A)
+        for (int B = 0; B < 8; ++B)
+          for (int d = 0; d < NC; ++d)
+            for (int e = 0; e < NC; ++e) {
+              double v = 0.0;
+              for (int a = 0; a < 8; ++a) {
+                const double wa = cellhost::child_weight(c, a, A);
+                if (wa == 0.0) continue;
+                for (int b = 0; b < 8; ++b) {
+                  const double wb = cellhost::child_weight(c, b, B);
+                  if (wb != 0.0) v += wa * wb * fixed_block[(a * NC + d) * R + b * NC + e];
+                }
+              }
+              G[(size_t)c * R * R + (A * NC + d) * R + B * NC + e] = (T)v;
+            }
+    CKS(h->arena.alloc(&mg.childm, (size_t)8 * R * R));
+    CK(cudaMemcpy(mg.childm, G.data(), G.size() * sizeof(T), cudaMemcpyHostToDevice));
+  }
   mg.lv.clear();
   Level<T> L0;
   L0.nx = h->nx;
@@ -450,7 +473,7 @@ int fill_mg(cell_handle* h, BlockMG<T>& mg) {
     Level<T>& L = mg.lv[l];
     if (l > 0) {
       Level<T>& F = mg.lv[l - 1];
-      if (l == 1) cell::galerkin<T, NC>(mg.fixedm, rho_of<T>(h), nullptr, L.ke, L.nx, L.ny, L.nz, h->st);
+      if (l == 1) cell::galerkin_child<T, NC>(mg.childm, rho_of<T>(h), L.ke, L.nx, L.ny, L.nz, h->st);
       else cell::galerkin<T, NC>(nullptr, nullptr, F.ke, L.ke, L.nx, L.ny, L.nz, h->st);
       cell::diag_inv<T, NC>(nullptr, nullptr, L.ke, L.dinv, L.nx, L.ny, L.nz, h->st);
       cell::stencil_from_elem<T, NC>(L.ke, L.st, L.nx, L.ny, L.nz, h->st);
@@ -512,7 +535,8 @@ int fill_mg(cell_handle* h, BlockMG<T>& mg) {
 // x = V-cycle approximation of A_l^-1 b (zero initial guess).  Chebyshev
 // coefficients are read from the level's device table (see fill_mg).
 template <typename T, int NC>
-void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64 xs, const int* mask) {
+void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64 xs, const int* mask,
+            bool started = false) {
   Level<T>& L = mg.lv[l];
   const i64 ws = NC * L.nn;
   if (L.coarsest && L.dense) {
@@ -521,8 +545,8 @@ void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64
   }
   const int deg = L.deg;
   cell::ApplyArgs<T> a{};
-  // pre-smoothing from x = 0
-  cell::cheb_init<T, NC>(b, bs, L.r, ws, L.d, ws, L.dinv, L.cc + 1, L.nn, 9, mask, h->st);
+  // pre-smoothing from x = 0 (started: the restriction already wrote r, d)
+  if (!started) cell::cheb_init<T, NC>(b, bs, L.r, ws, L.d, ws, L.dinv, L.cc + 1, L.nn, 9, mask, h->st);
   T* d = L.d;
   T* d2 = L.d2;
   int zero = 1;
@@ -540,8 +564,13 @@ void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64
   if (L.coarsest) return;
   Level<T>& C = mg.lv[l + 1];
   const i64 cs = NC * C.nn;
-  cell::restrict_fw<T, NC>(L.r, ws, C.b, cs, L.nx, L.ny, L.nz, 9, mask, h->st);
-  vcycle<T, NC>(h, mg, l + 1, C.b, cs, C.x, cs, mask);
+  if (C.coarsest && C.dense) {
+    cell::restrict_fw<T, NC>(L.r, ws, C.b, cs, L.nx, L.ny, L.nz, 9, mask, h->st);
+    vcycle<T, NC>(h, mg, l + 1, C.b, cs, C.x, cs, mask);
+  } else {
+    cell::restrict_init<T, NC>(L.r, ws, C.b, C.r, C.d, cs, C.dinv, C.cc + 1, L.nx, L.ny, L.nz, 9, mask, h->st);
+    vcycle<T, NC>(h, mg, l + 1, C.b, cs, C.x, cs, mask, true);
+  }
   cell::prolong_add<T, NC>(C.x, cs, x, xs, L.nx, L.ny, L.nz, 9, mask, h->st);
   // post-smoothing
   a = cell::ApplyArgs<T>{};

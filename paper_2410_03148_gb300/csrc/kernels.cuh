@@ -152,6 +152,14 @@ template <typename T, int NC> void axpy_view(T* x, i64 xs, const T* d, i64 ds, i
                                              const int* active, cudaStream_t s);
 template <typename T, int NC> void restrict_fw(const T* rf, i64 rs, T* bc, i64 bs, int nx, int ny,
                                                int nz, int nrhs, const int* active, cudaStream_t s);
+// restrict_fw that also starts the coarse level's Chebyshev smoothing:
+// bc = R rf, rc = bc, dc = (*c2p) Dinv bc (all with load stride cs)
+template <typename T, int NC> void restrict_init(const T* rf, i64 rs, T* bc, T* rc, T* dc, i64 cs,
+                                                 const T* dinv, const T* c2p, int nx, int ny, int nz,
+                                                 int nrhs, const int* active, cudaStream_t s);
+// level-1 coarse element matrices sum_c rho_c G_c (G: 8 child matrices, entry-major)
+template <typename T, int NC> void galerkin_child(const T* G, const T* rho, T* kec, int ncx, int ncy,
+                                                  int ncz, cudaStream_t s);
 template <typename T, int NC> void prolong_add(const T* xc, i64 cs, T* xf, i64 fs, int nx, int ny,
                                                int nz, int nrhs, const int* active, cudaStream_t s);
 // Galerkin coarse element matrices.  Fine level given either as fixed matrix

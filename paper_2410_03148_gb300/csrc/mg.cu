@@ -44,9 +44,12 @@ __global__ void k_axpy_view(T* __restrict__ x, i64 xs, const T* __restrict__ d, 
 
 // Full weighting (transpose of trilinear interpolation) on a periodic grid
 // whose fine sizes nx, ny, nz are even; coarse node I sits on fine node 2I.
+// With r and d set, the coarse level's Chebyshev start is written in the
+// same pass: r = b, d = c2 Dinv b (what cheb_init would do next).
 template <typename T, int NC>
 __global__ void k_restrict(const T* __restrict__ rf, i64 rs, T* __restrict__ bc, i64 bs, int nx,
-                           int ny, int nz, const int* active) {
+                           int ny, int nz, const int* active, T* __restrict__ rc, T* __restrict__ dc,
+                           const T* __restrict__ dinv, const T* __restrict__ c2p) {
   const int q = blockIdx.y;
   if (active && !active[q]) return;
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
@@ -73,6 +76,14 @@ __global__ void k_restrict(const T* __restrict__ rf, i64 rs, T* __restrict__ bc,
       }
 #pragma unroll
   for (int c = 0; c < NC; ++c) bc[q * bs + c * ncn + m] = acc[c];
+  if (rc) {
+    const T c2 = *c2p;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      rc[q * bs + c * ncn + m] = acc[c];
+      dc[q * bs + c * ncn + m] = c2 * dinv[c * ncn + m] * acc[c];
+    }
+  }
 }
 
 template <typename T, int NC>
@@ -170,6 +181,29 @@ __global__ void k_galerkin(const T* __restrict__ fixedm, const T* __restrict__ r
   for (int col = 0; col < R; ++col) kec[(i64)(row * R + col) * nce + E] = out[col];
 }
 
+// Level-1 coarse element matrices when every fine element matrix is
+// rho_e K: K_E = sum over the 8 children c of rho_c G_c with the fixed
+// G_c = P_c^T K P_c (computed once per material and grid on the host).
+// Thread per (coarse element, matrix entry); blockIdx.y = entry.
+template <typename T, int NC>
+__global__ void k_galerkin_child(const T* __restrict__ G, const T* __restrict__ rho, T* __restrict__ kec,
+                                 int ncx, int ncy, int ncz) {
+  constexpr int R = 8 * NC;
+  const i64 nce = (i64)ncx * ncy * ncz;
+  const i64 E = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  const int entry = blockIdx.y;
+  if (E >= nce) return;
+  const int nx = 2 * ncx, ny = 2 * ncy;
+  const int I = (int)(E % ncx), J = (int)((E / ncx) % ncy), K = (int)(E / ((i64)ncx * ncy));
+  T out = T(0);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const i64 fe = (2 * I + (c & 1)) + (i64)nx * ((2 * J + ((c >> 1) & 1)) + (i64)ny * (2 * K + (c >> 2)));
+    out = fma(rho[fe], G[c * R * R + entry], out);
+  }
+  kec[(i64)entry * nce + E] = out;
+}
+
 template <typename T, int NC>
 __global__ void k_diag_inv(const T* __restrict__ fixedm, const T* __restrict__ rho,
                            const T* __restrict__ ke, T* __restrict__ dinv, int nx, int ny, int nz) {
@@ -264,7 +298,15 @@ template <typename T, int NC>
 void restrict_fw(const T* rf, i64 rs, T* bc, i64 bs, int nx, int ny, int nz, int nrhs,
                  const int* active, cudaStream_t s) {
   const i64 ncn = (i64)(nx / 2) * (ny / 2) * (nz / 2);
-  note_launch(), k_restrict<T, NC><<<dim3(nblocks(ncn), nrhs), kB, 0, s>>>(rf, rs, bc, bs, nx, ny, nz, active);
+  note_launch(), k_restrict<T, NC><<<dim3(nblocks(ncn), nrhs), kB, 0, s>>>(rf, rs, bc, bs, nx, ny, nz, active,
+                                                                          nullptr, nullptr, nullptr, nullptr);
+}
+template <typename T, int NC>
+void restrict_init(const T* rf, i64 rs, T* bc, T* rc, T* dc, i64 cs, const T* dinv, const T* c2p, int nx,
+                   int ny, int nz, int nrhs, const int* active, cudaStream_t s) {
+  const i64 ncn = (i64)(nx / 2) * (ny / 2) * (nz / 2);
+  note_launch(), k_restrict<T, NC><<<dim3(nblocks(ncn), nrhs), kB, 0, s>>>(rf, rs, bc, cs, nx, ny, nz, active,
+                                                                          rc, dc, dinv, c2p);
 }
 template <typename T, int NC>
 void prolong_add(const T* xc, i64 cs, T* xf, i64 fs, int nx, int ny, int nz, int nrhs,
@@ -277,6 +319,12 @@ void galerkin(const T* fixedm, const T* rho, const T* kef, T* kec, int ncx, int 
               cudaStream_t s) {
   const i64 nce = (i64)ncx * ncy * ncz;
   note_launch(), k_galerkin<T, NC><<<dim3(nblocks(nce, 128), 8 * NC), 128, 0, s>>>(fixedm, rho, kef, kec, ncx, ncy, ncz);
+}
+template <typename T, int NC>
+void galerkin_child(const T* G, const T* rho, T* kec, int ncx, int ncy, int ncz, cudaStream_t s) {
+  const i64 nce = (i64)ncx * ncy * ncz;
+  note_launch(), k_galerkin_child<T, NC><<<dim3(nblocks(nce, 128), 64 * NC * NC), 128, 0, s>>>(G, rho, kec, ncx,
+                                                                                             ncy, ncz);
 }
 template <typename T, int NC>
 void diag_inv(const T* fixedm, const T* rho, const T* ke, T* dinv, int nx, int ny, int nz,
@@ -305,6 +353,9 @@ void dense_solve(const T* Ainv, int n, const T* b, i64 bs, T* x, i64 xs, i64 nn,
   template void prolong_add<T, NC>(const T*, i64, T*, i64, int, int, int, int, const int*,          \
                                    cudaStream_t);                                                   \
   template void galerkin<T, NC>(const T*, const T*, const T*, T*, int, int, int, cudaStream_t);     \
+  template void galerkin_child<T, NC>(const T*, const T*, T*, int, int, int, cudaStream_t);         \
+  template void restrict_init<T, NC>(const T*, i64, T*, T*, T*, i64, const T*, const T*, int, int, int, \
+                                     int, const int*, cudaStream_t);                                \
   template void diag_inv<T, NC>(const T*, const T*, const T*, T*, int, int, int, cudaStream_t);     \
   template void elem_lmax<T, NC>(const T*, i64, unsigned int*, cudaStream_t);
 INST_NC(float, 1)
