@@ -536,7 +536,7 @@ int fill_mg(cell_handle* h, BlockMG<T>& mg) {
 // coefficients are read from the level's device table (see fill_mg).
 template <typename T, int NC>
 void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64 xs, const int* mask,
-            bool started = false) {
+            bool started = false, const T** pending = nullptr) {
   Level<T>& L = mg.lv[l];
   const i64 ws = NC * L.nn;
   if (L.coarsest && L.dense) {
@@ -564,14 +564,15 @@ void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64
   if (L.coarsest) return;
   Level<T>& C = mg.lv[l + 1];
   const i64 cs = NC * C.nn;
+  const T* dpend = nullptr;   // coarse level's last direction, folded into the prolongation
   if (C.coarsest && C.dense) {
     cell::restrict_fw<T, NC>(L.r, ws, C.b, cs, L.nx, L.ny, L.nz, 9, mask, h->st);
     vcycle<T, NC>(h, mg, l + 1, C.b, cs, C.x, cs, mask);
   } else {
     cell::restrict_init<T, NC>(L.r, ws, C.b, C.r, C.d, cs, C.dinv, C.cc + 1, L.nx, L.ny, L.nz, 9, mask, h->st);
-    vcycle<T, NC>(h, mg, l + 1, C.b, cs, C.x, cs, mask, true);
+    vcycle<T, NC>(h, mg, l + 1, C.b, cs, C.x, cs, mask, true, &dpend);
   }
-  cell::prolong_add<T, NC>(C.x, cs, x, xs, L.nx, L.ny, L.nz, 9, mask, h->st);
+  cell::prolong_add<T, NC>(C.x, cs, x, xs, L.nx, L.ny, L.nz, 9, mask, h->st, dpend);
   // post-smoothing
   a = cell::ApplyArgs<T>{};
   a.x = x; a.xs = xs; a.b = b; a.bs = bs; a.y = L.r; a.ys = ws; a.dout = L.d; a.ds = ws;
@@ -586,7 +587,8 @@ void vcycle(cell_handle* h, BlockMG<T>& mg, int l, const T* b, i64 bs, T* x, i64
     level_apply<T, NC>(h, mg, l, cell::AM_CHEB, a, mask);
     std::swap(d, d2);
   }
-  cell::axpy_view<T, NC>(x, xs, d, ws, L.nn, 9, mask, h->st);
+  if (pending) *pending = d;   // the caller adds it while prolongating x
+  else cell::axpy_view<T, NC>(x, xs, d, ws, L.nn, 9, mask, h->st);
 }
 
 // k V-cycles by residual correction: x ~ A^-1 b.

@@ -161,7 +161,8 @@ template <typename T, int NC> void restrict_init(const T* rf, i64 rs, T* bc, T* 
 template <typename T, int NC> void galerkin_child(const T* G, const T* rho, T* kec, int ncx, int ncy,
                                                   int ncz, cudaStream_t s);
 template <typename T, int NC> void prolong_add(const T* xc, i64 cs, T* xf, i64 fs, int nx, int ny,
-                                               int nz, int nrhs, const int* active, cudaStream_t s);
+                                               int nz, int nrhs, const int* active, cudaStream_t s,
+                                               const T* dc = nullptr);
 // Galerkin coarse element matrices.  Fine level given either as fixed matrix
 // (device pointer to (8NC)^2 values) times rho, or as per-element SoA matrices.
 template <typename T, int NC> void galerkin(const T* fixedm, const T* rho, const T* kef, T* kec,

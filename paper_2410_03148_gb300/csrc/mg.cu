@@ -86,9 +86,11 @@ __global__ void k_restrict(const T* __restrict__ rf, i64 rs, T* __restrict__ bc,
   }
 }
 
+// xf += P (xc [+ dc]): with dc set, the coarse level's last smoothing
+// direction is folded in here instead of a separate xc += dc pass.
 template <typename T, int NC>
 __global__ void k_prolong_add(const T* __restrict__ xc, i64 cs, T* __restrict__ xf, i64 fs, int nx,
-                              int ny, int nz, const int* active) {
+                              int ny, int nz, const int* active, const T* __restrict__ dc) {
   const int q = blockIdx.y;
   if (active && !active[q]) return;
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
@@ -113,7 +115,7 @@ __global__ void k_prolong_add(const T* __restrict__ xc, i64 cs, T* __restrict__ 
       for (int a2 = 0; a2 < nxs; ++a2) {
         const i64 m = ii[a2] + (i64)cx * (jj[b2] + (i64)cy * kk[c2]);
 #pragma unroll
-        for (int c = 0; c < NC; ++c) acc[c] += xc[q * cs + c * ncn + m];
+        for (int c = 0; c < NC; ++c) acc[c] += xc[q * cs + c * ncn + m] + (dc ? dc[q * cs + c * ncn + m] : T(0));
       }
   const T w = wx * wy * wz;
 #pragma unroll
@@ -310,9 +312,10 @@ void restrict_init(const T* rf, i64 rs, T* bc, T* rc, T* dc, i64 cs, const T* di
 }
 template <typename T, int NC>
 void prolong_add(const T* xc, i64 cs, T* xf, i64 fs, int nx, int ny, int nz, int nrhs,
-                 const int* active, cudaStream_t s) {
+                 const int* active, cudaStream_t s, const T* dc) {
   const i64 nfn = (i64)nx * ny * nz;
-  note_launch(), k_prolong_add<T, NC><<<dim3(nblocks(nfn), nrhs), kB, 0, s>>>(xc, cs, xf, fs, nx, ny, nz, active);
+  note_launch(), k_prolong_add<T, NC><<<dim3(nblocks(nfn), nrhs), kB, 0, s>>>(xc, cs, xf, fs, nx, ny, nz, active,
+                                                                              dc);
 }
 template <typename T, int NC>
 void galerkin(const T* fixedm, const T* rho, const T* kef, T* kec, int ncx, int ncy, int ncz,
@@ -351,7 +354,7 @@ void dense_solve(const T* Ainv, int n, const T* b, i64 bs, T* x, i64 xs, i64 nn,
   template void restrict_fw<T, NC>(const T*, i64, T*, i64, int, int, int, int, const int*,          \
                                    cudaStream_t);                                                   \
   template void prolong_add<T, NC>(const T*, i64, T*, i64, int, int, int, int, const int*,          \
-                                   cudaStream_t);                                                   \
+                                   cudaStream_t, const T*);                                         \
   template void galerkin<T, NC>(const T*, const T*, const T*, T*, int, int, int, cudaStream_t);     \
   template void galerkin_child<T, NC>(const T*, const T*, T*, int, int, int, cudaStream_t);         \
   template void restrict_init<T, NC>(const T*, i64, T*, T*, T*, i64, const T*, const T*, int, int, int, \
