@@ -503,7 +503,13 @@ void multidot(const T* V, i64 vstride, i64 rstride, int nv, const T* w, i64 wstr
       return;
     }
   }
-  // one group of up to 16 vectors per block (w read once), else groups of 8
+  // one vector (norms): a single accumulator; up to 16 vectors: one group
+  // per block (w read once); else groups of 8
+  if (nv == 1) {
+    note_launch(), k_multidot<T, 1><<<dim3(nblk, nrhs, 1), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride,
+                                                                       len, partial, nvmax, active);
+    return;
+  }
   if (nv <= 16) {
     note_launch(), k_multidot<T, 16><<<dim3(nblk, nrhs, 1), kB, 0, s>>>(V, vstride, rstride, nv, w, wstride,
                                                                         len, partial, nvmax, active);
