@@ -90,7 +90,7 @@ __device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const Nod
 // Slots are shared by handles with equal matrices (reference counted, per
 // device); kernel parameters remain the fallback when all slots are taken.
 constexpr int kSlots = 4;
-__constant__ float c_k0[kSlots][1024];
+__constant__ __align__(16) float c_k0[kSlots][1024];   // 16-byte rows: read as float2 pairs too
 __constant__ float c_s0[kSlots][64];
 
 template <typename T, int NCM>
@@ -205,6 +205,82 @@ __global__ void __launch_bounds__(kBlock) k_apply_fixed_cslot(const ApplyArgs<fl
   // the single-component (local Schur) operator takes three loads per thread
   apply_fixed_pre_body<float, NCM, NCI, NCO, R0, C0, NEGLAST, MODE, (NCI == 1 ? 3 : 1)>(
       a, ConstCoef<SLOT, NCM>{});
+}
+
+// Packed-FP32 apply of K0 rows R0 .. R0+NCO-1 to all four input components
+// (the full operator Ahat), one (node, load) per thread.  Blackwell's paired
+// FMA (two FP32 multiply-adds per issued instruction) halves the issue cost of
+// the 1024-term element contraction, which bounds the scalar kernel at ~86 %
+// issue use.  Operand pairs are components (0, 1) and (2, 3) of a neighbour
+// against the matching adjacent coefficients of a K0 row; each element's pair
+// sum is scaled by rho_e with one paired FMA and the halves are added at the
+// end.  Capped at 96 registers (five 128-thread blocks per SM).  The same
+// pairing measured no gain for the three-component elastic block in its
+// Chebyshev modes, which keep the scalar kernel.
+template <int SLOT, int NCO, int R0, bool NEGLAST, int MODE>
+__global__ void __launch_bounds__(kBlock, 5) k_apply_k0_pk(const ApplyArgs<float> a) {
+  const int r = blockIdx.z;
+  if (r >= a.nrhs || (a.active && !a.active[r])) return;
+  const int nx = a.nx, ny = a.ny;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nx * ny) return;
+  const int j = p / nx;
+  const int i = p - j * nx;
+  const int k = blockIdx.y;
+  const int nxy = nx * ny;
+  const int xo[3] = {i == 0 ? nx - 1 : i - 1, i, i == nx - 1 ? 0 : i + 1};
+  const int yo[3] = {(j == 0 ? ny - 1 : j - 1) * nx, j * nx, (j == ny - 1 ? 0 : j + 1) * nx};
+  const int zo[3] = {(k == 0 ? a.nz - 1 : k - 1) * nxy, k * nxy, (k == a.nz - 1 ? 0 : k + 1) * nxy};
+  NodeIdx t;
+  t.nn = (i64)nxy * a.nz;
+  t.n = (i64)k * nxy + p;
+  const float* X[4];
+#pragma unroll
+  for (int d = 0; d < 4; ++d) X[d] = a.x + r * a.xs + d * t.nn;
+  float2 x01[27], x23[27];
+#pragma unroll
+  for (int q = 0; q < 27; ++q) {
+    const int m = xo[q % 3] + yo[(q / 3) % 3] + zo[q / 9];
+    x01[q] = make_float2(__ldg(X[0] + m), __ldg(X[1] + m));
+    x23[q] = make_float2(__ldg(X[2] + m), __ldg(X[3] + m));
+  }
+  const float2* K = reinterpret_cast<const float2*>(c_k0[SLOT]);
+  float2 acc[NCO];
+#pragma unroll
+  for (int c = 0; c < NCO; ++c) acc[c] = make_float2(0.f, 0.f);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
+    const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+    const float w = __ldg(a.rho + (xo[ex] + yo[ey] + zo[ez]));
+    float2 tl[NCO];
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) tl[c] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int q = (ex + (b & 1)) + 3 * (ey + ((b >> 1) & 1)) + 9 * (ez + (b >> 2));
+#pragma unroll
+      for (int c = 0; c < NCO; ++c) {
+        const int row = (la * 4 + R0 + c) * 16 + b * 2;   // float2 index of K0[4la+R0+c][4b]
+        tl[c] = __ffma2_rn(K[row], x01[q], tl[c]);
+        tl[c] = __ffma2_rn(K[row + 1], x23[q], tl[c]);
+      }
+    }
+    const float2 w2 = make_float2(w, w);
+#pragma unroll
+    for (int c = 0; c < NCO; ++c) acc[c] = __ffma2_rn(w2, tl[c], acc[c]);
+  }
+  float out[NCO], dold[NCO];
+#pragma unroll
+  for (int c = 0; c < NCO; ++c) {
+    out[c] = acc[c].x + acc[c].y;
+    // this node's own input (neighbour 13), used by the Chebyshev modes
+    dold[c] = (MODE == AM_CHEB || MODE == AM_CHEB_LAST) ? (c < 2 ? (c ? x01[13].y : x01[13].x)
+                                                               : (c == 3 ? x23[13].y : x23[13].x))
+                                                        : 0.f;
+  }
+  if (NEGLAST) out[NCO - 1] = -out[NCO - 1];
+  epilogue<float, NCO, MODE>(a, r, t, out, dold);
 }
 
 // Fixed-matrix operator, FP64: neighbours are loaded per element (FP64
@@ -570,6 +646,15 @@ void launch_cslot(const ApplyArgs<float>& a0, int nrhs, cudaStream_t s) {
   a.nrhs = nrhs;
   const int groups = (nrhs + RG - 1) / RG;
   const dim3 g = grid_for(a, groups);
+  if constexpr (NCM == 4 && NCI == 4 && C0 == 0) {
+    switch (a.cslot1 - 1) {
+      case 0: note_launch(), k_apply_k0_pk<0, NCO, R0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+      case 1: note_launch(), k_apply_k0_pk<1, NCO, R0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+      case 2: note_launch(), k_apply_k0_pk<2, NCO, R0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+      default: note_launch(), k_apply_k0_pk<3, NCO, R0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
+    }
+    return;
+  }
   switch (a.cslot1 - 1) {
     case 0: note_launch(), k_apply_fixed_cslot<0, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
     case 1: note_launch(), k_apply_fixed_cslot<1, NCM, NCI, NCO, R0, C0, NEG, MODE><<<g, kBlock, 0, s>>>(a); break;
