@@ -189,6 +189,15 @@ def cpu_sample(n_target, sample_n=16, reps=1, seed0=0):
     return per, per * scale * 1e3
 
 
+def workload_config(args, world):
+    """The workload keys both arms report (the GPU arm adds its timing notes)."""
+    n = args.n
+    return {"workload": f"{n}^3 periodic piezoelectric cell ({4 * n ** 3} dof), 9 loads, "
+                        "seeded Gaussian level sets, PZT-5H-class",
+            "tol": args.tol, "inner_tol": args.inner_tol,
+            "precision": args.precision, "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -207,9 +216,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.n}^3 periodic piezoelectric cell, 9 loads, seeded "
-                                "Gaussian level sets, PZT-5H-class",
-                   "l2": "working set > L2"},
+        "config": {**workload_config(args, int(os.environ.get("WORLD_SIZE", "1"))),
+                   "l2": "host cores: FP64 direct solves, no GPU"},
         "cpu_baseline": {"value": ms, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"one {sample_n}^3 cell per step (SuperLU direct solve, single "
                                    f"thread), time scaled by the dof ratio {scale:.0f}"},
@@ -395,10 +403,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == 1 else "f64", "data": "synthetic",
-            "config": {"workload": f"{n}^3 periodic piezoelectric cell ({4 * nn} dof), 9 loads, "
-                                   "seeded Gaussian level sets, PZT-5H-class",
-                       "tol": args.tol, "inner_tol": args.inner_tol,
-                       "precision": args.precision, "parallelism": f"replicas x{world}",
+            "config": {**workload_config(args, world),
                        "handle": "allocated once per process outside the timed region; each step = "
                                  "cell_update (rho, multigrid hierarchy) + solve + homogenise + "
                                  "d_h sensitivities",
