@@ -6,9 +6,11 @@
 // No thread writes another node's value, so there are no atomics and results
 // are bitwise reproducible.  For fixed-matrix operators (level 0: w_e = rho_e,
 // K = a block of the 32x32 element matrix K0 or the 8x8 local Schur matrix S0)
-// the matrix is a by-value kernel parameter, so every multiply-add reads its
-// coefficient straight from the constant bank.  Coarse multigrid levels carry
-// one Galerkin matrix per element, stored entry-major (coalesced).
+// the matrix sits in a __constant__ slot (or, when all slots are taken, in a
+// by-value kernel parameter), so every multiply-add reads its coefficient
+// straight from the constant bank; the full operator pairs its multiply-adds
+// (two FP32 FMAs per instruction).  Coarse multigrid levels carry one Galerkin
+// matrix per element, stored entry-major (coalesced), or an assembled stencil.
 //
 // Operator definitions: Eq. (sym-piezo) and its nonsymmetric second form
 // (potential rows negated), §2.5; block operators of P_SCP, §2.5.3.

@@ -69,14 +69,16 @@ def make_cell(design, kind, **opt):
     return Cell(torch.as_tensor(np.ascontiguousarray(design), device=dev()), MAT, kind=kind, **opt)
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 6, 7), (16, 16, 16), (2, 3, 2)])
+@pytest.mark.parametrize("shape", [(4, 4, 4), (5, 6, 7), (16, 16, 16), (2, 3, 2), (3, 17, 23)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_apply_matches_oracle_matvec(shape, dtype):
+    """All nine loads; (3, 17, 23) spans four 128-node blocks of an xy plane
+    with a ragged last block."""
     rho = cellgen.random_rho(shape, seed=1)
     cell = make_cell(rho, "rho")
     P = fem.CellProblem(rho, *MAT)
     rng = np.random.default_rng(2)
-    x = rng.standard_normal((3, 4) + shape)
+    x = rng.standard_normal((9, 4) + shape)
     y = cell.apply(torch.as_tensor(x, device=dev(), dtype=dtype)).double().cpu().numpy()
     yref = from_dof(negate_phi_rows(P.Kg @ to_dof(x)), shape)
     tol = 1e-12 if dtype == torch.float64 else 2e-6
