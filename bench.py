@@ -45,7 +45,7 @@ UNIT = "ms per 64^3 cell solve (9 loads, setup+solve+C^H+d_h sensitivities)"
 
 # Algorithmic cost per (node, load) of each timed kernel class of the library:
 # (flops, bytes, bound, dtype).  Bytes count one read of every input and one
-# write of every output (see the design doc for the derivation).
+# write of every output.
 CLASS_COST = {
     "full32": (2 * (1024 + 32), 4 * 4 + 4 * 4 + 4 / 9, "alu", "f32"),
     "full64": (2 * (1024 + 32), 8 * 4 + 8 * 4 + 8 + 8 / 9, "alu", "f64"),

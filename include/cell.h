@@ -104,7 +104,7 @@ typedef struct cell_options {
   int tensor_cores;    /* MIXED: 0 = SIMT FP32 applies only; 1 = fine-grid smoothing applies
                           of both preconditioner blocks (A and Sbar) on tcgen05 tensor
                           cores (TF32 element contraction, FP32 accumulate), used where
-                          nx % 8 == 0 and nx <= 128; 2 = also the Krylov operator Ahat
+                          nx % 8 == 0 and nx <= 64; 2 = also the Krylov operator Ahat
                           (3xTF32 split, FP32-accurate), used where nx % 16 == 0,
                           ny % 4 == 0, nz % 2 == 0. */
   int const_bank;      /* MIXED: nonzero (default) = FP32 element matrices in one of 4
@@ -308,19 +308,24 @@ int cell_get_rho(cell_handle* h, double* out);
 int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]);
 
 /* Homogenised tensors like cell_homogenise, but from fields the caller passes
- * and without allocating any device memory (the paper has no counterpart; this
- * serves callers that cannot allocate at that point, e.g. code being captured
- * into a CUDA graph or running under an allocator that forbids cudaMalloc).
+ * and without allocating any device memory (the paper has no counterpart).
+ * It serves callers that cannot allocate when they need the tensors: a
+ * framework whose caching allocator owns the device-memory budget and forbids
+ * allocation outside its pools, or a real-time loop that must not stall on
+ * the driver's allocator (cudaMalloc may synchronise the device).
  * d gives the grid, material and stream (d->input and d->opt are unused).
  * rho: N element scales; bhat, y, rhat: 9 FP64 cell vectors each (9*4*N
  * values): the right-hand sides as from cell_rhs, the solutions as from
- * cell_get_solution, and the residuals bhat - Ahat y; all DEVICE pointers.
+ * cell_get_solution, and the residuals bhat - Ahat y; all DEVICE pointers on
+ * the current device, which must also own d->stream (else CELL_EINVAL).
  * Block partial sums live in one fixed device array inside the library
- * (672 KB, held on every GPU that loads it), shared by all calls: calls that
- * overlap on the GPU race and must be ordered (e.g. issued on one stream).
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  Synchronises d->stream.
- * CELL_EINVAL for null pointers, sizes < 2, or more than 4,194,304 nodes. */
+ * (83,195 doubles = 665,560 bytes, held on every GPU that loads it until the
+ * process exits), shared by all calls: calls that overlap on the GPU race and
+ * must be ordered (e.g. issued on one stream).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress).  The call copies
+ * its three reductions to the host and synchronises d->stream before it
+ * returns.  CELL_EINVAL for null pointers, sizes < 2, or more than 4,194,304
+ * nodes; CELL_ECUDA if a launch or copy fails. */
 int cell_homogenise_noalloc(const cell_desc* d, const double* rho, const double* bhat,
                             const double* y, const double* rhat, double CH[36], double eH[18],
                             double kH[9]);

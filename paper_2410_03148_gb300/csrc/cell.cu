@@ -37,6 +37,14 @@ void set_error(const char* what, cudaError_t e = cudaSuccess) {
   }
 }
 
+}  // namespace
+
+namespace cell {
+void report_error(const char* what, cudaError_t e) { set_error(what, e); }
+}  // namespace cell
+
+namespace {
+
 #define CK(call)                                     \
   do {                                               \
     cudaError_t _e = (call);                         \
@@ -237,7 +245,6 @@ struct cell_handle {
   double* rho64 = nullptr;
   double* drho = nullptr;   // level-set input: d rho_e / d phi_e (§2.6 smoothing)
   double* gtmp = nullptr;   // level-set input: element sensitivities before the chain
-  double* K0dev = nullptr;
   double *b64 = nullptr, *x64 = nullptr, *r64 = nullptr;
   // mixed path: x64 as FP32 pairs and rho's low part, for the double-float residual
   float *xh = nullptr, *xl = nullptr, *rho_l = nullptr, *rho_tmp = nullptr;
@@ -967,8 +974,6 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
     CK(cudaMemcpy(h->zb, zb.data(), zb.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
   for (int i = 0; i < 1024; ++i) h->kf.K0.k[i] = (float)h->K0[i];
-  CKS(A.alloc(&h->K0dev, 1024));
-  CK(cudaMemcpyAsync(h->K0dev, h->K0, 1024 * sizeof(double), cudaMemcpyHostToDevice, h->st));
   h->kd.rho = h->rho64;
   CKS(A.alloc(&h->b64, 9 * len));
   CKS(A.alloc(&h->x64, 9 * len));
@@ -1110,6 +1115,72 @@ int solve_impl(cell_handle* h, cell_stats* st) {
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+
+namespace {
+// Upstream gradients in SI units -> the nondimensional G of g_e = sum G_IJ
+// W^I.K0 W^J (H = [[C^H, -e^H^T], [-e^H, -kappa^H]] in scaled units).
+cell::SensParams sens_params(const cell_handle* h, const double dC[36], const double de[18],
+                             const double dk[9]) {
+  cell::SensParams P;
+  std::memcpy(P.Z, h->Z, sizeof(P.Z));
+  std::memset(P.G, 0, sizeof(P.G));
+  const double se = std::sqrt(h->C0 * h->k0);
+  for (int p = 0; p < 6; ++p)
+    for (int q = 0; q < 6; ++q) P.G[p * 9 + q] = dC ? h->C0 * dC[p * 6 + q] : 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int p = 0; p < 6; ++p) {
+      const double v = de ? -0.5 * se * de[i * 6 + p] : 0.0;
+      P.G[(6 + i) * 9 + p] = v;
+      P.G[p * 9 + 6 + i] = v;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) P.G[(6 + i) * 9 + 6 + j] = dk ? -h->k0 * dk[i * 3 + j] : 0.0;
+  return P;
+}
+
+// sym(G) = Q diag(lam) Q^T (host, FP64 Jacobi): the mode tables of the
+// sensitivity kernels.  Modes with |lam| <= 1e-15 max|lam| are dropped.
+template <typename T>
+void sens_modes(const cell_handle* h, const cell::SensParams& P, cell::SensQ* Q, cell::SensModes<T>* M) {
+  double Gs[81], lam[9], V[81];
+  for (int i = 0; i < 9; ++i)
+    for (int j = 0; j < 9; ++j) Gs[i * 9 + j] = 0.5 * (P.G[i * 9 + j] + P.G[j * 9 + i]);
+  cellhost::sym_eig(Gs, 9, lam, V);
+  double lmax = 0.0;
+  for (int k = 0; k < 9; ++k) lmax = std::max(lmax, std::fabs(lam[k]));
+  int R = 0;
+  std::memset(Q, 0, sizeof(*Q));
+  std::memset(M, 0, sizeof(*M));
+  for (int k = 0; k < 9; ++k) {
+    if (!(std::fabs(lam[k]) > 1e-15 * lmax)) continue;
+    for (int I = 0; I < 9; ++I) Q->q[I * 9 + R] = V[I * 9 + k];
+    M->lam[R] = (T)lam[k];
+    for (int a = 0; a < 32; ++a) {
+      double z = 0.0;
+      for (int I = 0; I < 9; ++I) z += P.Z[a * 9 + I] * V[I * 9 + k];
+      M->zq[a * 9 + R] = (T)z;
+    }
+    ++R;
+  }
+  Q->R = R;
+  M->R = R;
+  for (int a = 0; a < 32; ++a)
+    for (int b = 0; b < 32; ++b)
+      M->ku[a * 32 + b] = b == a ? (T)h->K0[a * 32 + a] : (b > a ? (T)(2.0 * h->K0[a * 32 + b]) : T(0));
+}
+
+// The mode fields (R x 4 x nn values) go to the Krylov basis, which is free
+// between solves: (m + 1) x 9 x 4nn values of the Krylov type >= 9 x 4nn doubles.
+template <typename T>
+void run_sensitivity(cell_handle* h, const cell::SensParams& P, T* g) {
+  cell::SensQ Q;
+  cell::SensModes<T> M;
+  sens_modes<T>(h, P, &Q, &M);
+  void* work = h->d.opt.precision == CELL_MIXED_FP32 ? (void*)h->kf.V : (void*)h->kd.V;
+  cell::sensitivity<T>(h->x64, h->rho64, Q, M, static_cast<T*>(work), g, h->nx, h->ny, h->nz, 0, h->st);
+}
+}  // namespace
+
 
 extern "C" {
 
@@ -1261,38 +1332,13 @@ int cell_homogenise(cell_handle* h, double CH[36], double eH[18], double kH[9]) 
   return CELL_OK;
 }
 
-namespace {
-// Upstream gradients in SI units -> the nondimensional G of g_e = sum G_IJ
-// W^I.K0 W^J (H = [[C^H, -e^H^T], [-e^H, -kappa^H]] in scaled units).
-cell::SensParams sens_params(const cell_handle* h, const double dC[36], const double de[18],
-                             const double dk[9]) {
-  cell::SensParams P;
-  std::memcpy(P.Z, h->Z, sizeof(P.Z));
-  std::memset(P.G, 0, sizeof(P.G));
-  const double se = std::sqrt(h->C0 * h->k0);
-  for (int p = 0; p < 6; ++p)
-    for (int q = 0; q < 6; ++q) P.G[p * 9 + q] = dC ? h->C0 * dC[p * 6 + q] : 0.0;
-  for (int i = 0; i < 3; ++i)
-    for (int p = 0; p < 6; ++p) {
-      const double v = de ? -0.5 * se * de[i * 6 + p] : 0.0;
-      P.G[(6 + i) * 9 + p] = v;
-      P.G[p * 9 + 6 + i] = v;
-    }
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) P.G[(6 + i) * 9 + 6 + j] = dk ? -h->k0 * dk[i * 3 + j] : 0.0;
-  return P;
-}
-}  // namespace
-
 int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18], const double dk[9],
                      void* g, int dtype) {
   if (!h || !g || (dtype != CELL_F32 && dtype != CELL_F64)) return CELL_EINVAL;
   if (!h->solved) return CELL_ESTATE;
   const cell::SensParams P = sens_params(h, dC, de, dk);
-  if (dtype == CELL_F32)
-    cell::sensitivity<float>(h->x64, h->rho64, h->K0dev, P, static_cast<float*>(g), h->nx, h->ny, h->nz, 0, h->st);
-  else
-    cell::sensitivity<double>(h->x64, h->rho64, h->K0dev, P, static_cast<double*>(g), h->nx, h->ny, h->nz, 0, h->st);
+  if (dtype == CELL_F32) run_sensitivity<float>(h, P, static_cast<float*>(g));
+  else run_sensitivity<double>(h, P, static_cast<double*>(g));
   CK(cudaGetLastError());
   return CELL_OK;
 }
@@ -1303,7 +1349,7 @@ int cell_sensitivity_phi(cell_handle* h, const double dC[36], const double de[18
   if (h->d.input_kind != CELL_INPUT_PHI || !h->drho) return CELL_EINVAL;
   if (!h->solved) return CELL_ESTATE;
   const cell::SensParams P = sens_params(h, dC, de, dk);
-  cell::sensitivity<double>(h->x64, h->rho64, h->K0dev, P, h->gtmp, h->nx, h->ny, h->nz, 0, h->st);
+  run_sensitivity<double>(h, P, h->gtmp);
   if (dtype == CELL_F32)
     cell::chain_phi<float>(h->gtmp, h->drho, h->nx, h->ny, h->nz, static_cast<float*>(g), h->st);
   else

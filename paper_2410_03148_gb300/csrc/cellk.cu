@@ -187,46 +187,68 @@ k_sum(const double* __restrict__ x, i64 n, double* __restrict__ partial) {
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// One warp per element; lane a owns local dof a = 4*node + comp.
-// g_e = sum_J (K0 W^J)_a (sum_I G_IJ W^I_a) summed over lanes.
+// Element sensitivities in the eigen-modes of the symmetric upstream weights
+// (sym(G) = Q diag(lam) Q^T):  g_e = sum_IJ G_IJ W_e^I.K0 W_e^J
+//                                 = sum_m lam_m X_e^m.K0 X_e^m,  X^m = sum_I Q_Im W^I.
+// Pass 1 forms the fluctuation part of every mode at the nodes (reads the
+// nine FP64 solutions once, coalesced); pass 2 gives each thread one element,
+// adds the affine part (Zbar Q, element-local) and evaluates the symmetric
+// quadratic forms with the upper triangle of K0 (528 multiply-adds per mode),
+// the coefficients being compile-time offsets into the parameter bank.
 template <typename T>
 __global__ void __launch_bounds__(kB)
-k_sens(const double* __restrict__ y, const double* __restrict__ rho, const double* __restrict__ K0,
-       const __grid_constant__ SensParams P, T* __restrict__ g, int nx, int ny, int nz,
-       int times_rho) {
-  __shared__ T Ks[32][33];
-  for (int t = threadIdx.x; t < 1024; t += kB) Ks[t / 32][t % 32] = (T)K0[t];
-  __syncthreads();
+k_sens_modes(const double* __restrict__ y, const __grid_constant__ SensQ Q, T* __restrict__ X,
+             i64 nn) {
+  const i64 n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int c = blockIdx.y;
+  double w[9];
+#pragma unroll
+  for (int I = 0; I < 9; ++I) w[I] = y[((i64)I * 4 + c) * nn + n];
+  for (int m = 0; m < Q.R; ++m) {
+    double v = 0.0;
+#pragma unroll
+    for (int I = 0; I < 9; ++I) v = fma(Q.q[I * 9 + m], w[I], v);
+    X[((i64)m * 4 + c) * nn + n] = (T)v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kB, sizeof(T) == 4 ? 2 : 1)
+k_sens_elem(const T* __restrict__ X, const double* __restrict__ rho,
+            const __grid_constant__ SensModes<T> P, T* __restrict__ g, int nx, int ny, int nz,
+            int times_rho) {
   const i64 nxy = (i64)nx * ny, nn = nxy * nz;
-  const i64 e = (i64)blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nn) return;
-  const int lane = threadIdx.x & 31;
-  const int ln = lane >> 2, comp = lane & 3;
   const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / nxy);
-  const int ni = (i + (ln & 1)) % nx, nj = (j + ((ln >> 1) & 1)) % ny, nk = (k + (ln >> 2)) % nz;
-  const i64 node = ni + nx * (nj + (i64)ny * nk);
-  T W[9];
+  // 32-bit node offsets: cell_setup admits at most 4e8 nodes, so 4 nn < 2^31
+  const int xo[2] = {i, i + 1 == nx ? 0 : i + 1};
+  const int yo[2] = {j * nx, (j + 1 == ny ? 0 : j + 1) * nx};
+  const int nxy32 = (int)nxy;
+  const int zo[2] = {k * nxy32, (k + 1 == nz ? 0 : k + 1) * nxy32};
+  const int nn32 = (int)nn;
+  T acc = T(0);
+  for (int m = 0; m < P.R; ++m) {
+    const T* Xm = X + (i64)m * 4 * nn;
+    T x[32];
 #pragma unroll
-  for (int J = 0; J < 9; ++J) W[J] = (T)(P.Z[lane * 9 + J] + y[((i64)J * 4 + comp) * nn + node]);
-  T U[9];
+    for (int a = 0; a < 8; ++a) {
+      const int node = xo[a & 1] + yo[(a >> 1) & 1] + zo[a >> 2];
 #pragma unroll
-  for (int J = 0; J < 9; ++J) U[J] = T(0);
-#pragma unroll 4
-  for (int b = 0; b < 32; ++b) {
-    const T kab = Ks[lane][b];
+      for (int c = 0; c < 4; ++c) x[4 * a + c] = __ldg(Xm + (c * nn32 + node)) + P.zq[(4 * a + c) * 9 + m];
+    }
+    T q = T(0);
 #pragma unroll
-    for (int J = 0; J < 9; ++J) U[J] = fma(kab, __shfl_sync(0xffffffffu, W[J], b), U[J]);
+    for (int a = 0; a < 32; ++a) {
+      T t = P.ku[a * 32 + a] * x[a];
+#pragma unroll
+      for (int b = a + 1; b < 32; ++b) t = fma(P.ku[a * 32 + b], x[b], t);
+      q = fma(x[a], t, q);
+    }
+    acc = fma(P.lam[m], q, acc);
   }
-  T part = T(0);
-#pragma unroll
-  for (int J = 0; J < 9; ++J) {
-    T vj = T(0);
-#pragma unroll
-    for (int I = 0; I < 9; ++I) vj = fma((T)P.G[I * 9 + J], W[I], vj);
-    part = fma(U[J], vj, part);
-  }
-  double tot = warp_sum((double)part);
-  if (lane == 0) g[e] = (T)(times_rho ? tot * rho[e] : tot);
+  g[e] = times_rho ? (T)(acc * rho[e]) : acc;
 }
 
 inline unsigned nb(i64 n) { return (unsigned)((n + kB - 1) / kB); }
@@ -319,11 +341,11 @@ void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, 
 }
 
 template <typename T>
-void sensitivity(const double* y, const double* rho, const double* K0dev, const SensParams& P, T* g,
-                 int nx, int ny, int nz, int times_rho, cudaStream_t s) {
+void sensitivity(const double* y, const double* rho, const SensQ& Q, const SensModes<T>& P, T* xwork,
+                 T* g, int nx, int ny, int nz, int times_rho, cudaStream_t s) {
   const i64 nn = (i64)nx * ny * nz;
-  note_launch(), k_sens<T><<<(unsigned)((nn + kWarps - 1) / kWarps), kB, 0, s>>>(y, rho, K0dev, P, g, nx, ny, nz,
-                                                                  times_rho);
+  if (Q.R > 0) note_launch(), k_sens_modes<T><<<dim3(nb(nn), 4), kB, 0, s>>>(y, Q, xwork, nn);
+  note_launch(), k_sens_elem<T><<<nb(nn), kB, 0, s>>>(xwork, rho, P, g, nx, ny, nz, times_rho);
 }
 
 template void ersatz<float>(const float*, int, int, int, double, double, float*, double*, double*, cudaStream_t);
@@ -334,9 +356,9 @@ template void hj_step<double>(const double*, const double*, int, int, int, doubl
 template void chain_phi<double>(const double*, const double*, int, int, int, double*, cudaStream_t);
 template void rho_copy<float>(const float*, i64, float*, double*, int*, cudaStream_t);
 template void rho_copy<double>(const double*, i64, float*, double*, int*, cudaStream_t);
-template void sensitivity<float>(const double*, const double*, const double*, const SensParams&,
-                                 float*, int, int, int, int, cudaStream_t);
-template void sensitivity<double>(const double*, const double*, const double*, const SensParams&,
-                                  double*, int, int, int, int, cudaStream_t);
+template void sensitivity<float>(const double*, const double*, const SensQ&, const SensModes<float>&,
+                                 float*, float*, int, int, int, int, cudaStream_t);
+template void sensitivity<double>(const double*, const double*, const SensQ&, const SensModes<double>&,
+                                  double*, double*, int, int, int, int, cudaStream_t);
 
 }  // namespace cell

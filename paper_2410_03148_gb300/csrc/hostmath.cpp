@@ -212,6 +212,47 @@ double jacobi_lmax(const double* M, int n) {
   return lm;
 }
 
+void sym_eig(const double* A, int n, double* lam, double* Q) {
+  double M[256];
+  for (int i = 0; i < n * n; ++i) M[i] = A[i];
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) Q[i * n + k] = i == k ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 64; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += M[i * n + j] * M[i * n + j];
+        if (i != j) off += M[i * n + j] * M[i * n + j];
+      }
+    if (off <= 1e-32 * tot) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = M[p * n + q];
+        if (apq == 0.0) continue;
+        // rotation angle that zeroes M[p][q]: tan(2t) = 2 apq / (aqq - app)
+        const double th = (M[q * n + q] - M[p * n + p]) / (2.0 * apq);
+        const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {   // columns p, q of M
+          const double mkp = M[k * n + p], mkq = M[k * n + q];
+          M[k * n + p] = c * mkp - s * mkq;
+          M[k * n + q] = s * mkp + c * mkq;
+        }
+        for (int k = 0; k < n; ++k) {   // rows p, q of M
+          const double mpk = M[p * n + k], mqk = M[q * n + k];
+          M[p * n + k] = c * mpk - s * mqk;
+          M[q * n + k] = s * mpk + c * mqk;
+        }
+        for (int k = 0; k < n; ++k) {   // accumulate Q <- Q J
+          const double qkp = Q[k * n + p], qkq = Q[k * n + q];
+          Q[k * n + p] = c * qkp - s * qkq;
+          Q[k * n + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  for (int k = 0; k < n; ++k) lam[k] = M[k * n + k];
+}
+
 int spd_inverse(double* A, int n) {
   std::vector<double> I(n * n, 0.0);
   for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;

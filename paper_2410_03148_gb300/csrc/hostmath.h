@@ -29,6 +29,11 @@ double jacobi_lmax(const double* M, int n);
 // Returns 0 on success, -1 if the matrix is not positive definite.
 int spd_inverse(double* A, int n);
 
+// Eigen-decomposition of a symmetric n x n matrix A (row-major, n <= 16) by
+// cyclic Jacobi rotations: A = Q diag(lam) Q^T, column k of Q (Q[i*n + k])
+// the eigenvector of lam[k].  A is not modified.
+void sym_eig(const double* A, int n, double* lam, double* Q);
+
 // Trilinear prolongation weight of coarse corner B for the fine local node a
 // of child element c (all in 0..7, corner index = x + 2y + 4z).
 double child_weight(int c, int a, int B);

@@ -11,6 +11,9 @@ namespace cell {
 
 typedef long long i64;
 
+// Record the failure that cell_last_error() reports to the calling thread.
+void report_error(const char* what, cudaError_t e);
+
 // Count of kernels launched by the library (cell_launch_count()).
 extern std::atomic<long long> g_launches;
 inline void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
@@ -29,6 +32,20 @@ struct RhsParams {
 struct SensParams {
   double Z[32 * 9];
   double G[81];
+};
+
+// Element sensitivities in eigen-modes of the symmetrised upstream weights
+// sym(G) = Q diag(lam) Q^T (modes with lam = 0 dropped): X^m = sum_I Q_Im W^I.
+struct SensQ {
+  double q[81];   // Q[I*9 + m]
+  int R;          // number of modes kept
+};
+template <typename T>
+struct SensModes {
+  T ku[1024];     // upper triangle of K0 (row-major), off-diagonal entries doubled
+  T zq[32 * 9];   // affine part of the modes at local dof a: (Zbar Q)[a*9 + m]
+  T lam[9];
+  int R;
 };
 
 // Fixed element matrix passed by value as a kernel parameter: (8*NCM)^2
@@ -238,9 +255,10 @@ void gram9(const double* u, const double* v, i64 nn, double* partial, int nblk, 
 // out[0] = sum of x[0..n) (or of the squares)  (device scalar)
 void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s,
                 int squares = 0);
-// g_e = (rho_e if times_rho) * sum_IJ G_IJ W_e^I . K0 W_e^J, W = Zbar + y_e
-template <typename T> void sensitivity(const double* y, const double* rho, const double* K0dev,
-                                       const SensParams& P, T* g, int nx, int ny, int nz,
-                                       int times_rho, cudaStream_t s);
+// g_e = (rho_e if times_rho) * sum_IJ G_IJ W_e^I . K0 W_e^J, W = Zbar + y_e,
+// evaluated as sum_m lam_m X^m.K0 X^m; xwork holds Q.R x 4 x nn values of T.
+template <typename T> void sensitivity(const double* y, const double* rho, const SensQ& Q,
+                                       const SensModes<T>& P, T* xwork, T* g, int nx, int ny,
+                                       int nz, int times_rho, cudaStream_t s);
 
 }  // namespace cell

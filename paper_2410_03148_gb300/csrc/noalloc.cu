@@ -1,18 +1,20 @@
 // Homogenisation reduction that allocates no device memory.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// homogenised tensors: code running while a CUDA graph is being captured,
-// allocators that forbid allocation outside their own pools, or real-time
-// loops that must not stall on the driver's allocator.  cell_homogenise
-// needs the workspace of a cell_handle (made by cell_setup, which
-// allocates); cell_homogenise_noalloc instead takes every field from the
-// caller and keeps its block partial sums in the fixed device array below.
+// homogenised tensors: a framework whose caching allocator owns the whole
+// device-memory budget and forbids allocation outside its pools, or a
+// real-time loop that must not stall on the driver's allocator (cudaMalloc
+// may synchronise the device).  cell_homogenise needs the workspace of a
+// cell_handle (made by cell_setup, which allocates); cell_homogenise_noalloc
+// instead takes every field from the caller and keeps its block partial sums
+// in the fixed device array below.  It copies the three reductions to the
+// host and synchronises the caller's stream before it returns.
 //
 // The array is part of the library image: every GPU that loads libcell.so
-// holds it (kScratchDoubles doubles, 672 KB) until the process exits.  All
-// calls share it, so calls that overlap on the GPU (different streams or
-// threads without ordering between them) race on it and give wrong results;
-// calls ordered on one stream are safe.  Each call overwrites every scratch
+// holds it (kScratchDoubles = 83,195 doubles, 665,560 bytes) until the
+// process exits.  All calls share it, so calls that overlap on the GPU
+// (different streams or threads without ordering between them) race on it and
+// give wrong results; calls ordered on one stream are safe.  Each call overwrites every scratch
 // word it later reads, so nothing has to be cleared between calls.
 #include <cuda_runtime.h>
 
@@ -82,6 +84,20 @@ extern "C" int cell_homogenise_noalloc(const cell_desc* d, const double* rho, co
       }
       H0e[I * 9 + J] = s;
     }
+  cudaStream_t s = static_cast<cudaStream_t>(d->stream);
+  // the scratch address is per device: the stream must belong to the current one
+  int cur = -1, sdev = -1;
+  cudaError_t e = cudaGetDevice(&cur);
+  if (e == cudaSuccess) e = cudaStreamGetDevice(s, &sdev);
+  if (e != cudaSuccess) {
+    cell::report_error("cell_homogenise_noalloc: device of the stream", e);
+    return CELL_ECUDA;
+  }
+  if (sdev != cur) {
+    cell::report_error("cell_homogenise_noalloc: the stream belongs to another device than the current one",
+                       cudaSuccess);
+    return CELL_EINVAL;
+  }
   double* scr = nullptr;
   const int st = scratch_address(&scr);
   if (st != CELL_OK) return st;
@@ -90,16 +106,25 @@ extern "C" int cell_homogenise_noalloc(const cell_desc* d, const double* rho, co
   double* g2 = g1 + 81;                          // 81
   double* srho = g2 + 81;                        // 1
   const int nblk = (int)std::min<long long>(kMaxBlocks, std::max<long long>(1, (4 * nn + kChunk - 1) / kChunk));
-  cudaStream_t s = static_cast<cudaStream_t>(d->stream);
   cell::sum_reduce(rho, nn, partial, nblk, srho, s);
   cell::gram9(bhat, y, nn, partial, nblk, g1, s);
   cell::gram9(y, rhat, nn, partial, nblk, g2, s);
-  double G1[81], G2[81], sr = 0.0;
-  if (cudaMemcpyAsync(G1, g1, sizeof(G1), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(G2, g2, sizeof(G2), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaMemcpyAsync(&sr, srho, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess)
+  // a failed launch is not sticky: without this check the copies below could
+  // return another call's sums left in the shared array
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    cell::report_error("cell_homogenise_noalloc: reduction launch", e);
     return CELL_ECUDA;
+  }
+  double G1[81], G2[81], sr = 0.0;
+  e = cudaMemcpyAsync(G1, g1, sizeof(G1), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(G2, g2, sizeof(G2), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sr, srho, sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cell::report_error("cell_homogenise_noalloc: copy of the reductions", e);
+    return CELL_ECUDA;
+  }
   // energy form H = (sum rho) Zbar^T K0 Zbar - b.y - y.r, symmetrised
   double H[81];
   for (int i = 0; i < 81; ++i) H[i] = sr * H0e[i] - G1[i] - G2[i];

@@ -1,9 +1,10 @@
 """The allocation-free homogenisation entry point, through the C ABI.
 
 cell_homogenise_noalloc serves callers that cannot allocate device memory
-when they need the tensors (for instance while a CUDA graph is being
-captured): it takes the fields from the caller and keeps its partial sums in
-a fixed device array inside the library.  Two calls in a row must both agree
+when they need the tensors (a framework whose caching allocator owns the
+device-memory budget, or a loop that must not stall on cudaMalloc): it takes
+the fields from the caller and keeps its partial sums in a fixed device array
+inside the library.  Two calls in a row must both agree
 with cell_homogenise on the same solved design.  This file is collected
 last, so a run that stops at the first failure has run everything else.
 """
