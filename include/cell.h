@@ -223,6 +223,21 @@ int cell_homogenise(cell_handle* h, double CH[36], double eH[18], double kH[9]);
 int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18],
                      const double dk[9], void* g, int dtype);
 
+/* Element-wise change of the same weighted energy between the solutions of two
+ * handles on one grid and material: g_e = sum_IJ G_IJ (W_h^I.K0 W_h^J -
+ * W_ref^I.K0 W_ref^J), G from dC, de, dk as in cell_sensitivity (no rho_e
+ * factor).  It is evaluated in FP64 as B(W_h + W_ref, W_h - W_ref) of the
+ * symmetric form B (polarisation), so its rounding scales with the difference
+ * of the two fields rather than with the energies: central differences of
+ * the homogenised tensors between nearby designs (sum_e rho_e g_e, with the
+ * changed rho of the perturbed element handled by the caller) keep their
+ * digits at small steps.  g: DEVICE array of nx*ny*nz doubles, written on h's
+ * stream (ref's stream is synchronised first if it differs).  CELL_EINVAL for
+ * different grids or materials, ref == h, or a restart length too short for
+ * the workspace; CELL_ESTATE unless both handles hold a solution. */
+int cell_energy_difference(cell_handle* h, const cell_handle* ref, const double dC[36],
+                           const double de[18], const double dk[9], double* g);
+
 /* Shape sensitivity on the level set: dL/dphi_n at every node (device
  * buffer g of nx*ny*nz values, node = i + nx*(j + ny*k), dtype CELL_F32 or
  * CELL_F64) for the same L as cell_sensitivity.  With the ersatz map of §2.6,
@@ -244,6 +259,29 @@ int cell_sensitivity_phi(cell_handle* h, const double dC[36], const double de[18
  * (NULL = legacy default stream).  CELL_EINVAL for bad sizes or pointers. */
 int cell_hj_step(const void* phi, const void* v, int nx, int ny, int nz, double dt, void* out, int dtype,
                  void* stream);
+
+/* Shape velocity for Eq. HJ by Hilbertian extension-regularisation and
+ * projection (§2.6: the paper uses the Hilbertian projection method for
+ * constrained optimisation and gives no formulas; this is the library's
+ * reading).  Inner product <u, v>_H = int alpha^2 grad u.grad v + u v on the
+ * periodic unit cell, discretised with the Q1 node basis (A = alpha^2 K + M).
+ * Inputs are nodal sensitivities (dual vectors, e.g. from
+ * cell_sensitivity_phi): dJ of the objective and dC[i] of ncons <= 8
+ * constraints with current values C[i].  With g = A^-1 d their Riesz
+ * representers, theta_k an H-orthonormal basis of the constraint
+ * representers (Gram-Schmidt, g_i = sum_k R_ki theta_k) and P g_J the
+ * objective representer made H-orthogonal to them, the velocity is
+ *   v = wJ P g_J / ||P g_J||_H + sum_k mu_k theta_k,   R^T mu = wC C,
+ * so that a step phi -= dt v |grad phi| lowers J to first order and moves each
+ * constraint by -dt wC C_i.  dJ, dC[i] (a HOST array of DEVICE pointers) and v
+ * are DEVICE arrays of nx*ny*nz doubles (node = i + nx*(j + ny*k)); C is host.
+ * info (host, may be NULL) receives ||P g_J||_H, the Chebyshev iterations used
+ * and mu_1..mu_ncons.  Uses the handle's grid, stream and Krylov workspace (so
+ * not concurrently with a solve of the same handle); synchronises the stream.
+ * CELL_EINVAL for alpha <= 0, null pointers, ncons > 8 or linearly dependent
+ * constraint sensitivities. */
+int cell_hilbert_velocity(cell_handle* h, double alpha, const double* dJ, const double* const* dC,
+                          const double* C, int ncons, double wJ, double wC, double* v, double* info);
 
 /* Hydrostatic strain coefficient d_h = d31 + d32 + d33 with d = e S, S = C^-1
  * (§2.3), and its gradient with respect to every entry of C (dC[36]) and

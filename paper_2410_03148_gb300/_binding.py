@@ -28,7 +28,7 @@ EXPORTS = [
     "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_solve_batch", "cell_homogenise",
     "cell_sensitivity", "cell_sensitivity_phi", "cell_hj_step",
     "cell_dh", "cell_figure", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
-    "cell_element_matrices", "cell_homogenise_noalloc", "cell_launch_count", "cell_destroy",
+    "cell_element_matrices", "cell_homogenise_noalloc", "cell_energy_difference", "cell_hilbert_velocity", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
 ]
 
@@ -97,6 +97,9 @@ def load(path: str = LIB_PATH):
     lib.cell_homogenise.argtypes = [P, D, D, D]
     lib.cell_sensitivity.argtypes = [P, D, D, D, P, C.c_int]
     lib.cell_sensitivity_phi.argtypes = [P, D, D, D, P, C.c_int]
+    lib.cell_energy_difference.argtypes = [P, P, D, D, D, P]
+    lib.cell_hilbert_velocity.argtypes = [P, C.c_double, P, C.POINTER(C.c_void_p), D, C.c_int, C.c_double,
+                                          C.c_double, P, D]
     lib.cell_hj_step.argtypes = [P, P, C.c_int, C.c_int, C.c_int, C.c_double, P, C.c_int, P]
     lib.cell_dh.argtypes = [D, D, D, D, D]
     lib.cell_figure.argtypes = [C.c_int, D, D, D, D, D]
@@ -232,6 +235,24 @@ def cell_sensitivity(h, dC, de, dk, g_ptr: int, dtype: int):
 def cell_sensitivity_phi(h, dC, de, dk, g_ptr: int, dtype: int):
     keep, args = _grad_args(dC, de, dk)
     _check("cell_sensitivity_phi", load().cell_sensitivity_phi(h, *args, C.c_void_p(g_ptr), dtype))
+
+
+def cell_energy_difference(h, ref, dC, de, dk, g_ptr: int):
+    keep, args = _grad_args(dC, de, dk)
+    _check("cell_energy_difference", load().cell_energy_difference(h, ref, *args, C.c_void_p(g_ptr)))
+
+
+def cell_hilbert_velocity(h, alpha, dJ_ptr: int, dC_ptrs, Cvals, wJ, wC, v_ptr: int):
+    """Returns (||P g_J||_H, Chebyshev iterations, mu)."""
+    n = len(dC_ptrs)
+    ptrs = (C.c_void_p * max(n, 1))(*[C.c_void_p(p) for p in dC_ptrs])
+    cv = np.ascontiguousarray(np.asarray(Cvals, dtype=np.float64).reshape(n)) if n else np.zeros(1)
+    info = np.zeros(2 + max(n, 0))
+    _check("cell_hilbert_velocity",
+           load().cell_hilbert_velocity(h, float(alpha), C.c_void_p(dJ_ptr), ptrs,
+                                        cv.ctypes.data_as(C.POINTER(C.c_double)), n, float(wJ), float(wC),
+                                        C.c_void_p(v_ptr), info.ctypes.data_as(C.POINTER(C.c_double))))
+    return float(info[0]), int(info[1]), info[2:2 + n].copy()
 
 
 def cell_dh(Cm, em):

@@ -92,6 +92,30 @@ class Cell:
                            B.CELL_F32 if dtype == torch.float32 else B.CELL_F64)
         return g
 
+    def energy_difference(self, ref: "Cell", dC=None, de=None, dk=None) -> torch.Tensor:
+        """Element-wise change sum_IJ G_IJ (W^I.K0 W^J - W_ref^I.K0 W_ref^J)
+        between this handle's solution and ref's (FP64, polarisation form)."""
+        g = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        B.cell_energy_difference(self._h, ref._h, dC, de, dk, g.data_ptr())
+        return g
+
+    def hilbert_velocity(self, dJ: torch.Tensor, dCs=(), Cs=(), alpha=None, wJ=1.0, wC=1.0):
+        """Shape velocity of §2.6 (Hilbertian extension-regularisation and
+        projection) from nodal sensitivities (FP64 CUDA tensors of the grid's
+        shape); alpha defaults to 4 x the largest element size.  Returns
+        (v, ||P g_J||_H, Chebyshev iterations, mu)."""
+        if alpha is None:
+            alpha = 4.0 / min(self.shape)
+        ts = [dJ] + list(dCs)
+        for t in ts:
+            if not t.is_cuda or t.dtype != torch.float64 or tuple(t.shape) != self.shape:
+                raise ValueError("sensitivities must be float64 CUDA tensors of the grid's shape")
+        ts = [t.contiguous() for t in ts]
+        v = torch.empty(self.shape, dtype=torch.float64, device=self.device)
+        nP, its, mu = B.cell_hilbert_velocity(self._h, alpha, ts[0].data_ptr(), [t.data_ptr() for t in ts[1:]],
+                                              list(Cs), wJ, wC, v.data_ptr())
+        return v, nP, its, mu
+
     def sensitivity_phi(self, dC=None, de=None, dk=None, dtype=torch.float64) -> torch.Tensor:
         """dL/dphi at the nodes (shape (nz, ny, nx)) for a level-set handle."""
         g = torch.empty(self.shape, dtype=dtype, device=self.device)

@@ -550,59 +550,86 @@ __global__ void __launch_bounds__(kBlock) k_stencil(const T* __restrict__ ke, T*
     for (int d = 0; d < NC; ++d) st[(i64)((q * NC + c) * NC + d) * t.nn + t.n] = acc[q][d];
 }
 
-// Double-float helpers: exact product and sum error transformations.
-__device__ __forceinline__ void two_sum(float& s, float& lo, float p) {
-  const float t = s + p;
-  const float bb = t - s;
-  lo += (s - (t - bb)) + (p - bb);
+// Paired (two-lane) double-float steps: exact product error, TwoSum.
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ void two_sum2(float2& s, float2& lo, float2 p) {
+  const float2 m1 = f2(-1.f, -1.f);
+  const float2 t = __fadd2_rn(s, p);
+  const float2 bb = __ffma2_rn(s, m1, t);                       // t - s
+  const float2 e1 = __ffma2_rn(__ffma2_rn(bb, m1, t), m1, s);   // s - (t - bb)
+  const float2 e2 = __ffma2_rn(bb, m1, p);                      // p - bb
+  lo = __fadd2_rn(lo, __fadd2_rn(e1, e2));
   s = t;
 }
 
 // r = b - Ahat x with FP64-grade accuracy from FP32 arithmetic only.  One
-// thread per (node, output component, load): the compensated sum of each
-// row is one TwoSum chain, registers stay low and occupancy high.
+// thread per (node, load) computes the four rows: each element's 32 nodal
+// pairs (x = xh + xl) are loaded once and feed two row pairs, (0, 1) and
+// (2, 3), as paired FP32 operations.  Every product is error-free (FMA
+// residual) and every sum a TwoSum, per element and again after the rho_e
+// scaling (rho = rho_h + rho_l): the result carries about 2^-46 of the term
+// magnitudes, far below the residuals of the refinement loop.
 __global__ void __launch_bounds__(kBlock)
 k_resid_df(const float* __restrict__ xh, const float* __restrict__ xl, i64 xs,
            const double* __restrict__ b, i64 bs, double* __restrict__ r, i64 rs,
            const float* __restrict__ rho_h, const float* __restrict__ rho_l,
            const __grid_constant__ DFMat M, int nx, int ny, int nz, const int* active) {
-  const int q = blockIdx.z >> 2, c = blockIdx.z & 3;
+  const int q = blockIdx.z;
   if (active && !active[q]) return;
   NodeIdx t;
   if (!node_index(nx, ny, nz, t)) return;
   const float* XH = xh + q * xs;
   const float* XL = xl + q * xs;
-  float ah = 0.f, al = 0.f;
-#pragma unroll
+  const int nn32 = (int)t.nn;
+  const int xo[3] = {(int)t.xo[0], (int)t.xo[1], (int)t.xo[2]};
+  const int yo[3] = {(int)t.yo[0], (int)t.yo[1], (int)t.yo[2]};
+  const int zo[3] = {(int)t.zo[0], (int)t.zo[1], (int)t.zo[2]};
+  float2 ah[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, al[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
+#pragma unroll 1
   for (int e = 0; e < 8; ++e) {
     const int ex = e & 1, ey = (e >> 1) & 1, ez = e >> 2;
     const int la = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
-    const i64 el = t.xo[ex] + t.yo[ey] + t.zo[ez];
-    float sh = 0.f, sl = 0.f;
+    // corner offsets of this element by select (no dynamically indexed arrays)
+    const int x0 = ex ? xo[1] : xo[0], x1 = ex ? xo[2] : xo[1];
+    const int y0 = ey ? yo[1] : yo[0], y1 = ey ? yo[2] : yo[1];
+    const int z0 = ez ? zo[1] : zo[0], z1 = ez ? zo[2] : zo[1];
+    const int el = x0 + y0 + z0;
+    float2 sh[2] = {f2(0.f, 0.f), f2(0.f, 0.f)}, sl[2] = {f2(0.f, 0.f), f2(0.f, 0.f)};
 #pragma unroll
     for (int bn = 0; bn < 8; ++bn) {
-      const i64 m = t.xo[ex + (bn & 1)] + t.yo[ey + ((bn >> 1) & 1)] + t.zo[ez + (bn >> 2)];
+      const int m = ((bn & 1) ? x1 : x0) + (((bn >> 1) & 1) ? y1 : y0) + ((bn >> 2) ? z1 : z0);
 #pragma unroll
       for (int d = 0; d < 4; ++d) {
-        const float vh = __ldg(XH + d * t.nn + m), vl = __ldg(XL + d * t.nn + m);
-        const int k = (la * 4 + c) * 32 + bn * 4 + d;
-        const float kh = M.kh[k], kl = M.kl[k];
-        const float p = kh * vh;
-        const float pe = fmaf(kh, vh, -p);
-        two_sum(sh, sl, p);
-        sl = fmaf(kh, vl, fmaf(kl, vh, sl + pe));
+        const float vh = __ldg(XH + (d * nn32 + m)), vl = __ldg(XL + (d * nn32 + m));
+        const float2 vh2 = f2(vh, vh), vl2 = f2(vl, vl);
+#pragma unroll
+        for (int rp = 0; rp < 2; ++rp) {
+          const float2 kh = M.kh[(la * 2 + rp) * 32 + bn * 4 + d];
+          const float2 kl = M.kl[(la * 2 + rp) * 32 + bn * 4 + d];
+          const float2 p = __fmul2_rn(kh, vh2);
+          const float2 pe = __ffma2_rn(kh, vh2, f2(-p.x, -p.y));
+          two_sum2(sh[rp], sl[rp], p);
+          sl[rp] = __ffma2_rn(kh, vl2, __ffma2_rn(kl, vh2, __fadd2_rn(sl[rp], pe)));
+        }
       }
     }
     const float wh = __ldg(rho_h + el), wl = __ldg(rho_l + el);
-    const float p = sh * wh;
-    const float pe = fmaf(sh, wh, -p);
-    two_sum(ah, al, p);
-    al = fmaf(sh, wl, fmaf(sl, wh, al + pe));
+    const float2 wh2 = f2(wh, wh), wl2 = f2(wl, wl);
+#pragma unroll
+    for (int rp = 0; rp < 2; ++rp) {
+      const float2 p = __fmul2_rn(sh[rp], wh2);
+      const float2 pe = __ffma2_rn(sh[rp], wh2, f2(-p.x, -p.y));
+      two_sum2(ah[rp], al[rp], p);
+      al[rp] = __ffma2_rn(sh[rp], wl2, __ffma2_rn(sl[rp], wh2, __fadd2_rn(al[rp], pe)));
+    }
   }
-  double v = (double)ah + (double)al;
-  if (c == 3) v = -v;
-  const i64 o = (i64)c * t.nn + t.n;
-  r[q * rs + o] = b ? b[q * bs + o] - v : v;
+  const double v[4] = {(double)ah[0].x + (double)al[0].x, (double)ah[0].y + (double)al[0].y,
+                       (double)ah[1].x + (double)al[1].x, -((double)ah[1].y + (double)al[1].y)};
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const i64 o = (i64)c * t.nn + t.n;
+    r[q * rs + o] = b ? b[q * bs + o] - v[c] : v[c];
+  }
 }
 
 __global__ void k_axpy_split_f(double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,
@@ -778,8 +805,8 @@ void resid_df(const float* xh, const float* xl, i64 xs, const double* b, i64 bs,
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
-  note_launch(), k_resid_df<<<grid_for(a, 4 * nrhs), kBlock, 0, s>>>(xh, xl, xs, b, bs, r, rs, rho_h, rho_l, M,
-                                                                      nx, ny, nz, active);
+  note_launch(), k_resid_df<<<grid_for(a, nrhs), kBlock, 0, s>>>(xh, xl, xs, b, bs, r, rs, rho_h, rho_l, M,
+                                                                  nx, ny, nz, active);
 }
 
 __global__ void k_split(const double* __restrict__ x, float* __restrict__ xh, float* __restrict__ xl,

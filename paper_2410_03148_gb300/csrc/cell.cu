@@ -249,10 +249,11 @@ struct cell_handle {
   // mixed path: x64 as FP32 pairs and rho's low part, for the double-float residual
   float *xh = nullptr, *xl = nullptr, *rho_l = nullptr, *rho_tmp = nullptr;
   int* bad = nullptr;
+  const double** dptrs = nullptr;   // device pointer table of cell_hilbert_velocity
   int* tc_err = nullptr;   // tensor-core kernels: expired bounded waits
   bool tc_ok = false;      // grid tiles into tensor-core bricks
-  bool zm_ok = false;      // grid suits the z-marching tensor-core smoothers
-  float* zb = nullptr;     // their B operands: [ZK_UU | ZK_PP4][1024]
+  bool nc_ok = false;      // grid suits the node-centric tensor-core smoothers
+  float* ncb = nullptr;    // their B operands: [NK_UU | NK_SS4][nc_table_floats()]
   cell::TcTables tct;      // tensor-core operand tables (device)
   int cslot1 = 0;          // constant-bank slot of the FP32 element matrices (+1)
   cell::DFMat DF;
@@ -320,9 +321,9 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
   if (l == 0) {
     a.rho = K.rho;
     if constexpr (sizeof(T) == 4) {
-      const int kind = NC == 3 ? cell::ZK_UU : cell::ZK_PP4;
-      if (h->zm_ok && h->d.opt.tensor_cores >= 1 &&
-          cell::apply_zmarch(kind, a, h->zb + 1024 * kind, mode, 9, h->tc_err, h->st)) {
+      const int kind = NC == 3 ? cell::NK_UU : cell::NK_SS4;
+      if (h->nc_ok && h->d.opt.tensor_cores >= 1 &&
+          cell::apply_nc(kind, a, h->ncb + cell::nc_table_floats() * kind, mode, 9, h->tc_err, h->st)) {
       } else if constexpr (NC == 3) {
         cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
       } else {
@@ -930,10 +931,14 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   // the FP64 operator serves the refinement residual of the FP64 path
   std::memcpy(h->kd.K0.k, h->K0, sizeof(h->kd.K0.k));
   std::memcpy(h->kd.S0.k, h->S0, sizeof(h->kd.S0.k));
-  for (int i = 0; i < 1024; ++i) {
-    h->DF.kh[i] = (float)h->K0[i];
-    h->DF.kl[i] = (float)(h->K0[i] - (double)h->DF.kh[i]);
-  }
+  for (int la = 0; la < 8; ++la)
+    for (int rp = 0; rp < 2; ++rp)
+      for (int col = 0; col < 32; ++col) {
+        const double k0 = h->K0[(4 * la + 2 * rp) * 32 + col], k1 = h->K0[(4 * la + 2 * rp + 1) * 32 + col];
+        const float h0 = (float)k0, h1 = (float)k1;
+        h->DF.kh[(la * 2 + rp) * 32 + col] = make_float2(h0, h1);
+        h->DF.kl[(la * 2 + rp) * 32 + col] = make_float2((float)(k0 - (double)h0), (float)(k1 - (double)h1));
+      }
   // every device allocation of the handle happens here
   const i64 nn = h->nn;
   const i64 len = 4 * nn;
@@ -947,6 +952,7 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(A.alloc(&h->rho_l, nn));
   CKS(A.alloc(&h->rho_tmp, nn));
   CKS(A.alloc(&h->bad, 1));
+  CKS(A.alloc(&h->dptrs, 1 + cell::kHilbertMaxCons));
   CKS(A.alloc(&h->tc_err, 1));
   CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st));
   h->tc_ok = cell::tc_shape_ok(h->nx, h->ny, h->nz);
@@ -964,14 +970,15 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
     h->tct.b_full = dbf;
     h->tct.g_full = dgf;
   }
-  h->zm_ok = cell::zmarch_shape_ok(h->nx, h->ny, h->nz);
-  if (h->zm_ok) {
-    cell::zmarch_prepare();
-    std::vector<float> zb(2048);
-    cell::zmarch_build_b(cell::ZK_UU, h->K0, h->S0, zb.data());
-    cell::zmarch_build_b(cell::ZK_PP4, h->K0, h->S0, zb.data() + 1024);
-    CKS(A.alloc(&h->zb, zb.size()));
-    CK(cudaMemcpy(h->zb, zb.data(), zb.size() * sizeof(float), cudaMemcpyHostToDevice));
+  h->nc_ok = cell::nc_shape_ok(h->nx, h->ny, h->nz);
+  if (h->nc_ok) {
+    cell::nc_prepare();
+    const size_t nt = cell::nc_table_floats();
+    std::vector<float> tb(2 * nt);
+    cell::nc_build_b(cell::NK_UU, h->K0, h->S0, tb.data());
+    cell::nc_build_b(cell::NK_SS4, h->K0, h->S0, tb.data() + nt);
+    CKS(A.alloc(&h->ncb, tb.size()));
+    CK(cudaMemcpy(h->ncb, tb.data(), tb.size() * sizeof(float), cudaMemcpyHostToDevice));
   }
   for (int i = 0; i < 1024; ++i) h->kf.K0.k[i] = (float)h->K0[i];
   h->kd.rho = h->rho64;
@@ -1169,8 +1176,9 @@ void sens_modes(const cell_handle* h, const cell::SensParams& P, cell::SensQ* Q,
       M->ku[a * 32 + b] = b == a ? (T)h->K0[a * 32 + a] : (b > a ? (T)(2.0 * h->K0[a * 32 + b]) : T(0));
 }
 
-// The mode fields (R x 4 x nn values) go to the Krylov basis, which is free
-// between solves: (m + 1) x 9 x 4nn values of the Krylov type >= 9 x 4nn doubles.
+// The mode fields (R x 8 x nn floats or R x 4 x nn doubles, R <= 9) go to the
+// Krylov basis, which is free between solves: (m + 1) x 9 x 4nn values of the
+// Krylov type (m >= 1) hold 9 x 4nn doubles.
 template <typename T>
 void run_sensitivity(cell_handle* h, const cell::SensParams& P, T* g) {
   cell::SensQ Q;
@@ -1343,6 +1351,52 @@ int cell_sensitivity(cell_handle* h, const double dC[36], const double de[18], c
   return CELL_OK;
 }
 
+int cell_hilbert_velocity(cell_handle* h, double alpha, const double* dJ, const double* const* dC,
+                          const double* C, int ncons, double wJ, double wC, double* v, double* info) {
+  if (!h || !dJ || !v || !(alpha > 0.0) || !std::isfinite(alpha)) return CELL_EINVAL;
+  if (ncons < 0 || ncons > cell::kHilbertMaxCons || (ncons > 0 && (!dC || !C))) return CELL_EINVAL;
+  for (int i = 0; i < ncons; ++i)
+    if (!dC[i] || !std::isfinite(C[i])) return CELL_EINVAL;
+  if (!std::isfinite(wJ) || !std::isfinite(wC)) return CELL_EINVAL;
+  // workspace: 4 (1 + ncons) nn doubles of the Krylov basis ((m + 1) x 9 x 4 nn values)
+  const bool mixed = h->d.opt.precision == CELL_MIXED_FP32;
+  if ((mixed ? (h->d.opt.restart + 1) / 2 : h->d.opt.restart + 1) < 1) return CELL_EINVAL;
+  double* work = mixed ? reinterpret_cast<double*>(h->kf.V) : h->kd.V;
+  const int st = cell::hilbert_velocity(h->nx, h->ny, h->nz, alpha, dJ, dC, C, ncons, wJ, wC, v, work, h->dptrs,
+                                        h->partial, h->nblk, h->red, info, h->st);
+  if (st == CELL_ECUDA) set_error("cell_hilbert_velocity", cudaGetLastError());
+  if (st == CELL_EINVAL) set_error("cell_hilbert_velocity: constraint sensitivities are linearly dependent");
+  return st;
+}
+
+int cell_energy_difference(cell_handle* h, const cell_handle* ref, const double dC[36], const double de[18],
+                           const double dk[9], double* g) {
+  if (!h || !ref || !g || h == ref) return CELL_EINVAL;
+  if (h->nx != ref->nx || h->ny != ref->ny || h->nz != ref->nz) return CELL_EINVAL;
+  for (int i = 0; i < 1024; ++i)
+    if (h->K0[i] != ref->K0[i]) return CELL_EINVAL;
+  if (!h->solved || !ref->solved) return CELL_ESTATE;
+  // workspace: 2 x 9 x 4 nn doubles of h's Krylov basis ((m + 1) x 9 x 4 nn values)
+  const bool mixed = h->d.opt.precision == CELL_MIXED_FP32;
+  if ((mixed ? (h->d.opt.restart + 1) / 2 : h->d.opt.restart + 1) < 2) return CELL_EINVAL;
+  const cell::SensParams P = sens_params(h, dC, de, dk);
+  cell::SensQ Q;
+  cell::SensModes<double> M;
+  sens_modes<double>(h, P, &Q, &M);
+  cell::SensPair SP;
+  std::memcpy(SP.k, h->K0, sizeof(SP.k));
+  std::memcpy(SP.zq, M.zq, sizeof(SP.zq));
+  std::memcpy(SP.lam, M.lam, sizeof(SP.lam));
+  SP.R = M.R;
+  double* work = mixed ? reinterpret_cast<double*>(h->kf.V) : h->kd.V;
+  if (ref->st != h->st) {   // the reference's solution must be final on its own stream
+    CK(cudaStreamSynchronize(ref->st));
+  }
+  cell::energy_difference(h->x64, ref->x64, Q, SP, work, g, h->nx, h->ny, h->nz, h->st);
+  CK(cudaGetLastError());
+  return CELL_OK;
+}
+
 int cell_sensitivity_phi(cell_handle* h, const double dC[36], const double de[18], const double dk[9],
                          void* g, int dtype) {
   if (!h || !g || (dtype != CELL_F32 && dtype != CELL_F64)) return CELL_EINVAL;
@@ -1508,9 +1562,10 @@ int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs
     a.alpha = 1.f; a.rho = h->rho32; a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
     a.cslot1 = h->cslot1;   // the kernels the solver runs
     if (dtype == CELL_F32_TC) {
-      if (!h->zm_ok) return CELL_EINVAL;
-      const int kind = nc == 3 ? cell::ZK_UU : cell::ZK_PP4;
-      if (!cell::apply_zmarch(kind, a, h->zb + 1024 * kind, cell::AM_LINEAR, nrhs, h->tc_err, h->st))
+      if (!h->nc_ok) return CELL_EINVAL;
+      const int kind = nc == 3 ? cell::NK_UU : cell::NK_SS4;
+      if (!cell::apply_nc(kind, a, h->ncb + cell::nc_table_floats() * kind, cell::AM_LINEAR, nrhs,
+                          h->tc_err, h->st))
         return CELL_EINVAL;
     } else if (nc == 3) {
       cell::FixedMat<float, 4> M;

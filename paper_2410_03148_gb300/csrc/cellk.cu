@@ -191,10 +191,17 @@ k_sum(const double* __restrict__ x, i64 n, double* __restrict__ partial) {
 // (sym(G) = Q diag(lam) Q^T):  g_e = sum_IJ G_IJ W_e^I.K0 W_e^J
 //                                 = sum_m lam_m X_e^m.K0 X_e^m,  X^m = sum_I Q_Im W^I.
 // Pass 1 forms the fluctuation part of every mode at the nodes (reads the
-// nine FP64 solutions once, coalesced); pass 2 gives each thread one element,
-// adds the affine part (Zbar Q, element-local) and evaluates the symmetric
-// quadratic forms with the upper triangle of K0 (528 multiply-adds per mode),
-// the coefficients being compile-time offsets into the parameter bank.
+// nine FP64 solutions once, coalesced) and stores it as an FP32 pair
+// (hi, lo = v - hi) or in FP64.  Pass 2 gives each thread one element.  K0
+// annihilates a constant value per component (rigid translations, uniform
+// potential), so the element's values are first taken relative to its local
+// node 0: the nodal values are up to ~N times their variation across one
+// element, and forming the quadratic form from them directly in FP32 would
+// cancel that many digits.  The differences come from the pairs
+// (hi_a - hi_0) + (lo_a - lo_0); the affine part of the loads (Zbar Q, zero at
+// local node 0) is added, and the symmetric quadratic form is evaluated with
+// the upper triangle of K0 (528 multiply-adds per mode, the coefficients at
+// compile-time offsets of the parameter bank).
 template <typename T>
 __global__ void __launch_bounds__(kB)
 k_sens_modes(const double* __restrict__ y, const __grid_constant__ SensQ Q, T* __restrict__ X,
@@ -209,7 +216,13 @@ k_sens_modes(const double* __restrict__ y, const __grid_constant__ SensQ Q, T* _
     double v = 0.0;
 #pragma unroll
     for (int I = 0; I < 9; ++I) v = fma(Q.q[I * 9 + m], w[I], v);
-    X[((i64)m * 4 + c) * nn + n] = (T)v;
+    if constexpr (sizeof(T) == 4) {
+      const float hi = (float)v;
+      X[((i64)m * 8 + c) * nn + n] = hi;                       // hi parts: planes 0..3
+      X[((i64)m * 8 + 4 + c) * nn + n] = (float)(v - (double)hi);   // lo parts: planes 4..7
+    } else {
+      X[((i64)m * 4 + c) * nn + n] = (T)v;
+    }
   }
 }
 
@@ -222,21 +235,46 @@ k_sens_elem(const T* __restrict__ X, const double* __restrict__ rho,
   const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= nn) return;
   const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / nxy);
-  // 32-bit node offsets: cell_setup admits at most 4e8 nodes, so 4 nn < 2^31
-  const int xo[2] = {i, i + 1 == nx ? 0 : i + 1};
-  const int yo[2] = {j * nx, (j + 1 == ny ? 0 : j + 1) * nx};
-  const int nxy32 = (int)nxy;
-  const int zo[2] = {k * nxy32, (k + 1 == nz ? 0 : k + 1) * nxy32};
-  const int nn32 = (int)nn;
+  // 32-bit node offsets: cell_setup admits at most 4e8 nodes, so 8 nn < 2^32
+  const unsigned xo[2] = {(unsigned)i, (unsigned)(i + 1 == nx ? 0 : i + 1)};
+  const unsigned yo[2] = {(unsigned)(j * nx), (unsigned)((j + 1 == ny ? 0 : j + 1) * nx)};
+  const unsigned nxy32 = (unsigned)nxy;
+  const unsigned zo[2] = {(unsigned)k * nxy32, (unsigned)(k + 1 == nz ? 0 : k + 1) * nxy32};
+  const unsigned nn32 = (unsigned)nn;
   T acc = T(0);
   for (int m = 0; m < P.R; ++m) {
-    const T* Xm = X + (i64)m * 4 * nn;
     T x[32];
+    if constexpr (sizeof(T) == 4) {
+      const T* Xh = X + (i64)m * 8 * nn;
+      const T* Xl = Xh + 4 * (i64)nn;
+      float h0[4], l0[4];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int node = xo[a & 1] + yo[(a >> 1) & 1] + zo[a >> 2];
+      for (int c = 0; c < 4; ++c) {
+        h0[c] = __ldg(Xh + (c * nn32 + zo[0] + yo[0] + xo[0]));
+        l0[c] = __ldg(Xl + (c * nn32 + zo[0] + yo[0] + xo[0]));
+      }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) x[4 * a + c] = __ldg(Xm + (c * nn32 + node)) + P.zq[(4 * a + c) * 9 + m];
+      for (int a = 0; a < 8; ++a) {
+        const unsigned node = xo[a & 1] + yo[(a >> 1) & 1] + zo[a >> 2];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float dh = a ? __ldg(Xh + (c * nn32 + node)) - h0[c] : 0.f;
+          const float dl = a ? __ldg(Xl + (c * nn32 + node)) - l0[c] : 0.f;
+          x[4 * a + c] = (dh + dl) + P.zq[(4 * a + c) * 9 + m];
+        }
+      }
+    } else {
+      const T* Xm = X + (i64)m * 4 * nn;
+      T x0[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) x0[c] = __ldg(Xm + (c * nn32 + zo[0] + yo[0] + xo[0]));
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        const unsigned node = xo[a & 1] + yo[(a >> 1) & 1] + zo[a >> 2];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          x[4 * a + c] = (a ? __ldg(Xm + (c * nn32 + node)) - x0[c] : T(0)) + P.zq[(4 * a + c) * 9 + m];
+      }
     }
     T q = T(0);
 #pragma unroll
@@ -249,6 +287,82 @@ k_sens_elem(const T* __restrict__ X, const double* __restrict__ rho,
     acc = fma(P.lam[m], q, acc);
   }
   g[e] = times_rho ? (T)(acc * rho[e]) : acc;
+}
+
+// Energy difference of two solutions by the polarisation identity
+// B(W1, W1) - B(W2, W2) = B(W1 + W2, W1 - W2) for the symmetric bilinear form
+// B(U, V) = sum_IJ G_IJ U^I.K0 V^J = sum_m lam_m (Q^T U)_m.K0 (Q^T V)_m (FP64):
+// the difference field is formed first, so its rounding scales with the
+// difference, not with the energies.  Pass 1: the mode fields of the sum and
+// of the difference of the two fluctuation sets; pass 2: per element, both
+// taken relative to local node 0 (K0 annihilates constants), the sum gets
+// twice the affine part, and q = S.K0 D.
+__global__ void __launch_bounds__(kB)
+k_sens_modes_pair(const double* __restrict__ y1, const double* __restrict__ y2, const __grid_constant__ SensQ Q,
+                  double* __restrict__ XS, double* __restrict__ XD, i64 nn) {
+  const i64 n = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int c = blockIdx.y;
+  double ws[9], wd[9];
+#pragma unroll
+  for (int I = 0; I < 9; ++I) {
+    const double a = y1[((i64)I * 4 + c) * nn + n], b = y2[((i64)I * 4 + c) * nn + n];
+    ws[I] = a + b;
+    wd[I] = a - b;
+  }
+  for (int m = 0; m < Q.R; ++m) {
+    double vs = 0.0, vd = 0.0;
+#pragma unroll
+    for (int I = 0; I < 9; ++I) {
+      vs = fma(Q.q[I * 9 + m], ws[I], vs);
+      vd = fma(Q.q[I * 9 + m], wd[I], vd);
+    }
+    XS[((i64)m * 4 + c) * nn + n] = vs;
+    XD[((i64)m * 4 + c) * nn + n] = vd;
+  }
+}
+
+__global__ void __launch_bounds__(kB)
+k_sens_elem_pair(const double* __restrict__ XS, const double* __restrict__ XD,
+                 const __grid_constant__ SensPair P, double* __restrict__ g, int nx, int ny, int nz) {
+  const i64 nxy = (i64)nx * ny, nn = nxy * nz;
+  const i64 e = (i64)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  const int i = (int)(e % nx), j = (int)((e / nx) % ny), k = (int)(e / nxy);
+  const i64 xo[2] = {i, i + 1 == nx ? 0 : i + 1};
+  const i64 yo[2] = {(i64)j * nx, (i64)(j + 1 == ny ? 0 : j + 1) * nx};
+  const i64 zo[2] = {(i64)k * nxy, (i64)(k + 1 == nz ? 0 : k + 1) * nxy};
+  double acc = 0.0;
+  for (int m = 0; m < P.R; ++m) {
+    const double* S = XS + (i64)m * 4 * nn;
+    const double* D = XD + (i64)m * 4 * nn;
+    double sv[32], dv[32];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const i64 node = xo[a & 1] + yo[(a >> 1) & 1] + zo[a >> 2];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        sv[4 * a + c] = S[c * nn + node];
+        dv[4 * a + c] = D[c * nn + node];
+      }
+    }
+#pragma unroll
+    for (int a = 31; a >= 0; --a) {
+      const int c = a & 3;
+      sv[a] = sv[a] - sv[c] + 2.0 * P.zq[a * 9 + m];
+      dv[a] = dv[a] - dv[c];
+    }
+    double q = 0.0;
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      double t = 0.0;
+#pragma unroll
+      for (int b = 0; b < 32; ++b) t = fma(P.k[a * 32 + b], dv[b], t);
+      q = fma(sv[a], t, q);
+    }
+    acc = fma(P.lam[m], q, acc);
+  }
+  g[e] = acc;
 }
 
 inline unsigned nb(i64 n) { return (unsigned)((n + kB - 1) / kB); }
@@ -346,6 +460,15 @@ void sensitivity(const double* y, const double* rho, const SensQ& Q, const SensM
   const i64 nn = (i64)nx * ny * nz;
   if (Q.R > 0) note_launch(), k_sens_modes<T><<<dim3(nb(nn), 4), kB, 0, s>>>(y, Q, xwork, nn);
   note_launch(), k_sens_elem<T><<<nb(nn), kB, 0, s>>>(xwork, rho, P, g, nx, ny, nz, times_rho);
+}
+
+void energy_difference(const double* y1, const double* y2, const SensQ& Q, const SensPair& P, double* xwork,
+                       double* g, int nx, int ny, int nz, cudaStream_t s) {
+  const i64 nn = (i64)nx * ny * nz;
+  double* XS = xwork;
+  double* XD = xwork + (i64)9 * 4 * nn;
+  if (Q.R > 0) note_launch(), k_sens_modes_pair<<<dim3(nb(nn), 4), kB, 0, s>>>(y1, y2, Q, XS, XD, nn);
+  note_launch(), k_sens_elem_pair<<<nb(nn), kB, 0, s>>>(XS, XD, P, g, nx, ny, nz);
 }
 
 template void ersatz<float>(const float*, int, int, int, double, double, float*, double*, double*, cudaStream_t);

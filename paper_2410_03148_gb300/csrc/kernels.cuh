@@ -48,6 +48,15 @@ struct SensModes {
   int R;
 };
 
+// Energy difference of two solutions (FP64): the full K0, the affine part of
+// the modes and the eigenvalues of sym(G).
+struct SensPair {
+  double k[1024];
+  double zq[32 * 9];
+  double lam[9];
+  int R;
+};
+
 // Fixed element matrix passed by value as a kernel parameter: (8*NCM)^2
 // entries, row-major over local dofs NCM*node + comp.  Kernel parameters live
 // in the constant bank, so fully unrolled loops read the entries as FFMA/DFMA
@@ -117,10 +126,11 @@ template <typename T, int NC> void stencil_from_elem(const T* ke, T* st, int nx,
 
 // FP64-grade residual r = b - Ahat x (r = Ahat x if b is null) in FP32 double-float arithmetic: x is
 // given as FP32 pairs (x = xh + xl), K0 and rho likewise; products are
-// error-free (FMA), sums use TwoSum.  KH/KL: high/low FP32 parts of K0.
+// error-free (FMA), sums use TwoSum.  kh/kl: high/low FP32 parts of K0 as row
+// pairs, entry [(la * 2 + rp) * 32 + col] = (K0[4 la + 2 rp][col], K0[4 la + 2 rp + 1][col]).
 struct DFMat {
-  float kh[1024];
-  float kl[1024];
+  float2 kh[512];
+  float2 kl[512];
 };
 void resid_df(const float* xh, const float* xl, i64 xs, const double* b, i64 bs, double* r, i64 rs,
               const float* rho_h, const float* rho_l, const DFMat& M, int nx, int ny, int nz,
@@ -147,18 +157,19 @@ size_t tc_table_idx();
 void tc_build_tables_host(const double* K0, float* b_full, unsigned short* g_full);
 void apply_tc_full(const ApplyArgs<float>& a, const TcTables& T, int nrhs, int* err, cudaStream_t s);
 
-// Tensor-core fine-level smoother applies marching along z (apply_z.cu,
-// tcgen05 kind::tf32).  ZK_UU: elastic block A (3 -> 3) of one load per CTA;
-// ZK_PP4: local-Schur operator on four loads at once.  B tables (1024 floats
-// per kind) come from zmarch_build_b; zmarch_prepare() once per device before
-// launches or capture.  err counts expired bounded waits.
-enum { ZK_UU = 0, ZK_PP4 = 1 };
-bool zmarch_shape_ok(int nx, int ny, int nz);
-void zmarch_prepare();
-void zmarch_build_b(int kind, const double* K0, const double* S0, float* out);
-// Returns false (nothing launched) if a staged array is not 16-byte aligned.
-bool apply_zmarch(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
-                  cudaStream_t s);
+// Tensor-core fine-level smoother applies, node-centric (apply_nc.cu,
+// tcgen05 kind::tf32): NK_UU = elastic block A (3 -> 3) of one load per CTA,
+// NK_SS4 = local-Schur operator on four loads per CTA.  B tables
+// (nc_table_floats() floats per kind) come from nc_build_b; nc_prepare() once
+// per device before launches or capture.  err counts expired bounded waits.
+enum { NK_UU = 0, NK_SS4 = 1 };
+bool nc_shape_ok(int nx, int ny, int nz);
+void nc_prepare();
+size_t nc_table_floats();
+void nc_build_b(int kind, const double* K0, const double* S0, float* out);
+// Returns false (nothing launched) if the grid would exceed the launch limits.
+bool apply_nc(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
+              cudaStream_t s);
 
 // ---- multigrid helpers (mg.cu) ----------------------------------------------
 // r = b, d = c2 Dinv b with c2 read from device memory (*c2p)
@@ -231,7 +242,25 @@ template <typename T> void axpy_f64(double* x, i64 xs, const T* d, i64 ds, i64 l
                                     int nrhs, const int* active, cudaStream_t s);
 template <typename T> void fill(T* p, i64 n, T v, cudaStream_t s);
 
+// ---- shape velocity (hilbert.cu) ----------------------------------------------
+// Riesz representers in periodic H^1 (A = alpha^2 K + M, Chebyshev iteration
+// with exact spectral bounds), projection of the objective representer off
+// the constraint representers and the constraint correction; v (nn doubles).
+// work: 4 (1 + ncons) nn doubles; dptrs_dev: device room for 1 + ncons
+// pointers; partial / red as for reduce_partials; info (host, optional):
+// ||P g_J||_H, Chebyshev iterations, mu_1..mu_ncons.
+constexpr int kHilbertMaxCons = 8;
+int hilbert_velocity(int nx, int ny, int nz, double alpha, const double* dJ, const double* const* dC,
+                     const double* C, int ncons, double wJ, double wC, double* v, double* work,
+                     const double** dptrs_dev, double* partial, int nblk, double* red, double* info,
+                     cudaStream_t s);
+
 // ---- cell-level kernels (cellk.cu) -------------------------------------------
+// g_e = sum_IJ G_IJ (W1^I.K0 W1^J - W2^I.K0 W2^J) for two solution sets y1, y2
+// of one grid and material (W = Zbar + y), as B(W1 + W2, W1 - W2); xwork holds
+// 2 x 9 x 4 x nn doubles.
+void energy_difference(const double* y1, const double* y2, const SensQ& Q, const SensPair& P, double* xwork,
+                       double* g, int nx, int ny, int nz, cudaStream_t s);
 template <typename Tin> void ersatz(const Tin* phi, int nx, int ny, int nz, double rho_void,
                                     double eta, float* rho32, double* rho64, double* drho,
                                     cudaStream_t s);
@@ -256,7 +285,8 @@ void gram9(const double* u, const double* v, i64 nn, double* partial, int nblk, 
 void sum_reduce(const double* x, i64 n, double* partial, int nblk, double* out, cudaStream_t s,
                 int squares = 0);
 // g_e = (rho_e if times_rho) * sum_IJ G_IJ W_e^I . K0 W_e^J, W = Zbar + y_e,
-// evaluated as sum_m lam_m X^m.K0 X^m; xwork holds Q.R x 4 x nn values of T.
+// evaluated as sum_m lam_m X^m.K0 X^m; xwork holds Q.R x 8 x nn floats (T =
+// float: FP32 pairs of the mode fields) or Q.R x 4 x nn doubles.
 template <typename T> void sensitivity(const double* y, const double* rho, const SensQ& Q,
                                        const SensModes<T>& P, T* xwork, T* g, int nx, int ny,
                                        int nz, int times_rho, cudaStream_t s);

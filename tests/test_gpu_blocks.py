@@ -1,16 +1,18 @@
 """GPU parity of the preconditioner-block applies (§2.5.3: the elastic block A
 and Sbar = sum_e rho_e S0) against the FP64 oracle, through cell_apply_block.
 
-Three kernels: SIMT FP64 and FP32, and the z-marching tensor-core kernel
+Three kernels: SIMT FP64 and FP32, and the node-centric tensor-core kernel
 that the fine-level smoothers use (TF32 inputs, FP32 accumulation).
 Tolerances: FP64 1e-12 and FP32 2e-6 relative to max|K| max|x| x 8 (as the
 full-operator tests); TF32, component-wise: a TF32 input carries a relative
 error below 2^-10 (truncation of 13 mantissa bits), a TF32-rounded matrix
 entry below 2^-11, so every product term is within 2^-9 of its exact value
 and |y - y_ref| <= 2^-9 (|A| |x|)_i + FP32 accumulation (2e-6 |A||x|).
-Shapes are (nz, ny, nx); the tensor-core kernel needs nx % 8 == 0 and
-nx <= 64 and is covered with one tile (nx = 8), several tiles, the widest
-row (nx = 64), ragged 15-row y bricks and several z chunks.
+Shapes are (nz, ny, nx); the tensor-core kernel tiles nodes 8 (x) by 16 (y)
+inside CTAs of up to 32 x 16 nodes and a chunk of z planes, and masks ragged
+edges: the shapes cover one tile (nx = 8), several tiles per CTA, several
+CTAs along x, ragged x (nx = 7, 24, 40) and y (ny = 4, 17, 31), and several z
+chunks.
 """
 import numpy as np
 import pytest
@@ -61,7 +63,7 @@ def oracle_block(rho, block, x):
     return np.array(ys), np.array(bs), Ke
 
 
-SHAPES = [(3, 4, 8), (5, 17, 16), (7, 31, 24), (40, 16, 32), (4, 8, 64)]
+SHAPES = [(3, 4, 8), (5, 17, 16), (7, 31, 24), (40, 16, 32), (4, 8, 64), (3, 5, 7), (2, 18, 40)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -86,15 +88,6 @@ def test_block_apply_matches_oracle(shape, block, kind):
         assert err.max() < tol * np.abs(Ke).max() * np.abs(x).max() * 8
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 72), (4, 4, 12)])
-def test_block_apply_tc_rejects_unsupported_width(shape):
-    from paper_2410_03148_gb300._binding import CellError
-    cell = make_cell(cellgen.random_rho(shape, seed=16))
-    x = torch.zeros((1, 3) + shape, device=dev())
-    with pytest.raises(CellError):
-        cell.apply_block("A", x, tensor_cores=True)
-
-
 @pytest.mark.parametrize("block", ["A", "Sbar"])
 def test_block_apply_tc_is_reproducible(block):
     shape = (16, 16, 16)
@@ -106,12 +99,14 @@ def test_block_apply_tc_is_reproducible(block):
     assert torch.equal(y1, y2)
 
 
+@pytest.mark.parametrize("n", [64, 128])
 @pytest.mark.parametrize("block", ["A", "Sbar"])
-def test_block_apply_tc_64cube_sampled(block):
-    """64^3 (the benchmark grid, same launch configuration as the smoothers):
-    sampled nodes on tile, brick and chunk boundaries against the oracle's
-    node-by-node element sum."""
-    shape = (64, 64, 64)
+def test_block_apply_tc_sampled_full_size(block, n):
+    """64^3 and 128^3 (the benchmark grids, same launch configuration as the
+    smoothers): sampled nodes on tile, CTA and z-chunk boundaries (multiples of
+    8, 16 and 32 and their neighbours, both periodic ends) against the
+    oracle's node-by-node element sum, for loads 0, 4 and 8."""
+    shape = (n, n, n)
     rho = cellgen.random_rho(shape, seed=14)
     cell = make_cell(rho)
     nc = 3 if block == "A" else 1
@@ -120,9 +115,9 @@ def test_block_apply_tc_64cube_sampled(block):
     x = rng.standard_normal((nrhs, nc) + shape).astype(np.float32)
     y = cell.apply_block(block, torch.as_tensor(x, device=dev()), tensor_cores=True).double().cpu().numpy()
     Ke = precond.block_matrix(unit_K0(shape), block)
-    xs = [0, 1, 7, 8, 31, 32, 63]
-    ys = [0, 1, 14, 15, 16, 29, 30, 44, 45, 59, 60, 63]
-    zs = [0, 1, 10, 11, 12, 21, 22, 32, 62, 63]
+    edges = sorted({c for m in (0, 8, 16, 32, n // 2, n - 32, n - 16, n - 8) for c in (m - 1, m, m + 1)
+                    if 0 <= c < n} | {n - 1})
+    xs, ys, zs = edges, edges[::2], edges[1::3]
     nodes = [(i, j, k) for i in xs for j in ys for k in zs]
     for r in (0, 4, 8):
         want = precond.block_rows(rho, Ke, nc, x[r].astype(np.float64), nodes)

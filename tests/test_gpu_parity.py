@@ -494,22 +494,25 @@ def test_dh_gradient_matches_central_differences_64cube():
     interface, 0.01 < rho < 0.99, and 32 solid), each to 1e-5 relative.
 
     The difference quotient of d_h is taken through its linearisation at the
-    base design, grad d_h(H0) . (H+ - H-) / (2 step), which differs from
-    (d_h(H+) - d_h(H-)) / (2 step) by O(step^2).  H+ - H- is about 1e-11 of H
-    at this step, so it is not formed as the difference of the two energy sums
-    (FP64 rounding of H alone is 1e-16 of H): the rho-weighted element energies
-    of both solves, contracted with grad d_h (the sensitivity kernel's
-    quadratic forms times rho_e), are differenced element by element and
-    summed with compensated (math.fsum) summation.  The energy form is
-    stationary in the fluctuations, so solves to 1e-12 leave an O(1e-24)
-    error in each H."""
+    base design, grad d_h(H0) . (H+ - H-) / (rho+ - rho-), which differs from
+    (d_h(H+) - d_h(H-)) / (rho+ - rho-) by O(step^2).  H+ - H- is about 1e-11
+    of H at this step: it is formed neither as the difference of the two
+    energy sums nor of the element energies (FP64 rounding of the energies,
+    summed over 262,144 elements, is ~1e-17 of L: the size of the whole
+    difference for elements whose sensitivity is 1e-3 of the largest), but
+    element by element in the polarisation form B(W+ + W-, W+ - W-) of the
+    grad-d_h-weighted energy (cell_energy_difference), whose rounding scales
+    with W+ - W-, and summed with compensated (math.fsum) summation.  The energy
+    form is stationary in the fluctuations: a solve with residual r leaves an
+    error of order r.A^-1 r in each H, so the solves go to 1e-13."""
     import math
     from paper_2410_03148_gb300 import dh
     shape = (64, 64, 64)
     phi = cellgen.gaussian_levelset(shape, seed=0)
-    opts = dict(precision=0, tol=1e-12, max_iter=4000)
+    opts = dict(precision=0, tol=1e-13, max_iter=6000, max_refine=40)
     base = make_cell(phi, "phi", **opts)
-    base.solve()
+    st0 = base.solve(allow_notconv=True)
+    res = [max(st0["rel_residual"])]
     Ch, eh, _ = base.homogenise()
     d0, dC, de = dh(Ch, eh)
     g = base.sensitivity(dC, de, None).cpu().numpy().ravel()
@@ -519,24 +522,36 @@ def test_dh_gradient_matches_central_differences_64cube():
     inter = np.flatnonzero((r > 0.01) & (r < 0.99))
     solid = np.flatnonzero(r > 0.999)
     picks = list(rng.choice(inter, 32, replace=False)) + list(rng.choice(solid, 32, replace=False))
-    cell = make_cell(rho, "rho", **opts)
+    plus = make_cell(rho, "rho", **opts)
+    minus = make_cell(rho, "rho", **opts)
     step = 1e-6
     worst = 0.0
+    rows = []
     for e in picks:
-        parts = []
-        for sgn in (1, -1):
-            rp = r.copy()
-            rp[e] += sgn * step
-            cell.update(torch.as_tensor(rp.reshape(shape), device=dev()))
-            st = cell.solve()
-            assert max(st["rel_residual"]) <= 1e-12
-            w = cell.sensitivity(dC, de, None).cpu().numpy().ravel()
-            parts.append(rp * w)
-        fd = math.fsum((parts[0] - parts[1]).tolist()) / (2 * step)
+        rp, rm = r.copy(), r.copy()
+        rp[e] += step
+        rm[e] -= step
+        for c, rr in ((plus, rp), (minus, rm)):
+            c.update(torch.as_tensor(rr.reshape(shape), device=dev()))
+            st = c.solve(allow_notconv=True)
+            res.append(max(st["rel_residual"]))
+        # sum_e (rho+_e Q+_e - rho-_e Q-_e): rho+ = rho- except at e
+        dq = plus.energy_difference(minus, dC, de, None).cpu().numpy().ravel()
+        qp = plus.sensitivity(dC, de, None).cpu().numpy().ravel()[e]
+        qm = minus.sensitivity(dC, de, None).cpu().numpy().ravel()[e]
+        terms = r * dq
+        terms[e] = 0.5 * (rp[e] + rm[e]) * dq[e] + 0.5 * (rp[e] - rm[e]) * (qp + qm)
+        fd = math.fsum(terms.tolist()) / (rp[e] - rm[e])
         rel = abs(fd - g[e]) / abs(g[e])
         worst = max(worst, rel)
-        assert rel < 1e-5, (e, fd, g[e], rel)
-    print(f"64^3 d_h gradient vs central differences (64 elements, step 1e-6): max rel err {worst:.2e}")
+        rows.append((int(e), r[e], g[e], fd, rel))
+    print(f"\n64^3 d_h gradient vs central differences (64 elements, step 1e-6): max rel err {worst:.2e}, "
+          f"max rel residual {max(res):.1e}, |g| range {min(abs(x[2]) for x in rows):.2e}.."
+          f"{max(abs(x[2]) for x in rows):.2e}")
+    for row in sorted(rows, key=lambda x: -x[4])[:5]:
+        print("  element %d rho %.4f g %.6e fd %.6e rel %.2e" % row)
+    assert max(res) <= 1e-12
+    assert worst < 1e-5
 
 
 @pytest.mark.parametrize("precision", [0, 1])
