@@ -57,6 +57,11 @@ CLASS_COST = {
     "schur0": (2 * (64 + 8), 4 * (1 + 2 + 2 + 1) + 4 / 9 + 4 / 9, "hbm", "f32", 1),
     "coupling": (2 * (192 + 8), 4 * (3 + 1 + 1) + 4 / 9, "alu", "f32", 3),
 }
+# The tensor-core smoothers (node-centric TF32 MMAs): each (node, load) row
+# takes 15 MMAs of K = 8 against N = 32 columns, 2 x 120 x 32 flops; their
+# algorithmic bytes are those of the class above, which bound them (the MMA
+# work at the TF32 rate takes less time than the bytes at the HBM rate).
+TC_FLOPS_PER_ROW = 2 * 120 * 32
 # Algorithmic bytes per dof and load of the plain FP32 operator apply
 # (read x, write y, rho amortised over 4 dof x 9 loads)
 APPLY_BYTES_PER_DOF_RHS = 4 + 4 + 4 / 36
@@ -88,6 +93,10 @@ def parse():
     ap.add_argument("--accuracy-designs", type=int, default=2)
     # fine-grid smoothers on the tensor cores (node-centric tcgen05 TF32 kernels)
     ap.add_argument("--tensor-cores", type=int, default=1, choices=[0, 1, 2])
+    # E1 benchmark of the paper's weak-scaling study instead of the headline step
+    ap.add_argument("--e1", action="store_true")
+    # batched uneven cells (16 each of 32^3, 48^3, 64^3) instead of the headline step
+    ap.add_argument("--batch", action="store_true")
     return ap.parse_args()
 
 
@@ -126,6 +135,14 @@ def peaks():
             d = json.load(f)
         return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
     return 6800.0, "fallback", 2070.0
+
+
+def peaks_tf32():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f).get("bf16_tflops", 1900.0) / 2.0
+    return 1900.0 / 2.0
 
 
 class ClockSampler:
@@ -264,10 +281,112 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_e1(args):
+    """E1 benchmark (§2.5.4, Table 1): level set -prod cos(2 pi x_i) - 0.2, the
+    single load eps_bar^(11), outer tolerance 1e-8; SCP and DBP, FP64 and mixed,
+    1 and 2 V-cycles per block.  Prints one JSON line per configuration with
+    the GMRES iterations and the solve time (CUDA events around cell_solve)."""
+    import torch
+    import cellgen
+    from paper_2410_03148_gb300 import Cell, load
+    load()
+    dev = torch.device("cuda", 0)
+    mat = cellgen.pzt5h_class()
+    n = args.n
+    phi = torch.as_tensor(cellgen.e1_levelset(n), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for prec in (1, 0):
+        for pc in (0, 1):
+            for vc in (1, 2):
+                cell = Cell(phi, mat, kind="phi", precision=prec, precond=pc, load_mask=1, tol=1e-8,
+                            vcycles_u=vc, vcycles_phi=vc, tensor_cores=args.tensor_cores, max_iter=4000)
+                cell.solve()                   # warm-up (graph capture, first-touch)
+                ms = []
+                for _ in range(2):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    st = cell.solve()
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                print(json.dumps({"workload": f"E1 {n}^3 ({4 * n ** 3} dof), load eps11, tol 1e-8",
+                                  "precision": "mixed" if prec else "fp64",
+                                  "precond": "SCP" if pc == 0 else "DBP", "vcycles": vc,
+                                  "gmres_iters": st["iters"][0], "refinements": st["refinements"],
+                                  "rel_residual": st["rel_residual"][0], "solve_ms": min(ms)}), flush=True)
+                cell.close()
+                torch.cuda.empty_cache()
+
+
+def run_batch(args):
+    """Batched uneven cells: 48 seeded designs (16 each of 32^3, 48^3, 64^3), 9
+    loads each, mixed precision at the bench tolerance, solved by one
+    cell_solve_batch call (one stream per handle); against the same handles
+    solved one after another, and against one-by-one FP64 solves.  Prints one
+    JSON line with the three wall times (synchronised, host clock)."""
+    import numpy as np
+    import torch
+    import cellgen
+    from paper_2410_03148_gb300 import Cell, load, solve_batch
+    load()
+    dev = torch.device("cuda", 0)
+    mat = cellgen.pzt5h_class()
+    sizes = [32] * 16 + [48] * 16 + [64] * 16
+    phis = [torch.as_tensor(cellgen.gaussian_levelset(n, seed=s), device=dev) for s, n in enumerate(sizes)]
+    opt = dict(tol=args.tol, inner_tol=args.inner_tol, tensor_cores=args.tensor_cores)
+    cells = []
+    for phi in phis:
+        with torch.cuda.stream(torch.cuda.Stream(dev)):
+            cells.append(Cell(phi, mat, kind="phi", precision=1, **opt))
+    torch.cuda.synchronize()
+    solve_batch(cells)                 # warm-up: graph capture of every handle
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sts = solve_batch(cells)
+    torch.cuda.synchronize()
+    t_batch = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    for c in cells:
+        c.solve()
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    H = [c.homogenise() for c in cells]
+    for c in cells:
+        c.close()
+    del cells
+    torch.cuda.empty_cache()
+    t64 = 0.0
+    err = 0.0
+    for phi, h in zip(phis, H):
+        c = Cell(phi, mat, kind="phi", precision=0, tol=args.tol, max_iter=4000)
+        c.solve()                      # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        c.solve()
+        torch.cuda.synchronize()
+        t64 += time.perf_counter() - t0
+        for a, b in zip(h, c.homogenise()):
+            err = max(err, float(np.abs(a - b).max() / np.abs(b).max()))
+        c.close()
+    print(json.dumps({"workload": "48 designs: 16 each of 32^3, 48^3, 64^3 (seeds 0-47), 9 loads, mixed",
+                      "tol": args.tol, "batch_s": t_batch, "designs_per_s": len(sizes) / t_batch,
+                      "sequential_s": t_seq, "fp64_one_by_one_s": t64,
+                      "batch_speedup_vs_sequential": t_seq / t_batch, "batch_speedup_vs_fp64": t64 / t_batch,
+                      "max_iters": max(max(st["iters"]) for st in sts),
+                      "CH_eH_kH_block_rel_vs_fp64": err}), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.e1:
+        run_e1(args)
+        return
+    if args.batch:
+        run_batch(args)
         return
     import numpy as np
     import torch
@@ -359,6 +478,9 @@ def main():
     cnt = {c: sum(s["class_count"][c] for s in stats) for c in B.PROF_CLASSES}
     units = {c: sum(s["class_units"][c] for s in stats) for c in B.PROF_CLASSES}
     flops_u, bytes_u, bound, kdt, ndof = CLASS_COST[dom]
+    tc_class = args.tensor_cores >= 1 and prec == 1 and dom in ("elastic0", "schur0")
+    if tc_class:
+        bound = "hbm"
     nn = n ** 3
     avg_ms = tot[dom] / max(cnt[dom], 1)
     per_launch_units = units[dom] / max(cnt[dom], 1)
@@ -379,6 +501,14 @@ def main():
         roof["traffic"] = tt["bytes_per_node_load"] * nn * per_launch_units
         roof["traffic_source"] = (f"ncu dram__bytes_read+write of one {tt.get('n')}^3 launch "
                                   f"({tt.get('profile')}), per node and load, scaled to this launch")
+    if tc_class:
+        # tensor-pipe view: MMA flops per launch (the Schur kernel packs four loads per row)
+        rows = nn * per_launch_units / (4 if dom == "schur0" else 1)
+        tf32_peak = peaks_tf32()
+        roof["tensor_view"] = {"mma_tflops": TC_FLOPS_PER_ROW * rows / (avg_ms * 1e-3) / 1e12,
+                               "tf32_peak_tflops": tf32_peak,
+                               "frac": TC_FLOPS_PER_ROW * rows / (avg_ms * 1e-3) / 1e12 / tf32_peak,
+                               "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) / 2, the nominal TF32 ratio"}
     dof_rate = ndof * nn * per_launch_units / (avg_ms * 1e-3)
     roof.update({"kernel": dom,
                  "peak_source": (f"hbm {hbm_kind} (MEASURED_PEAKS.json)" if bound == "hbm" else

@@ -101,18 +101,24 @@ typedef struct cell_options {
   int coarse_dofs;     /* stop coarsening once a level has at most this many dofs */
   int load_mask;       /* bit I set = solve load I (default 0x1FF = all nine) */
   int profile;         /* nonzero: time kernel classes with CUDA events (cell_stats) */
-  int tensor_cores;    /* MIXED: 0 = SIMT FP32 applies only; 1 = fine-grid smoothing applies
-                          of both preconditioner blocks (A and Sbar) on tcgen05 tensor
-                          cores (TF32 element contraction, FP32 accumulate), used where
-                          nx % 8 == 0 and nx <= 64; 2 = also the Krylov operator Ahat
+  int tensor_cores;    /* MIXED: 0 = SIMT FP32 applies only; 1 (default) = fine-grid smoothing
+                          applies of both preconditioner blocks (A and Sbar) on tcgen05
+                          tensor cores: node-centric TF32 element contraction with FP32
+                          accumulation, any grid size; 2 = also the Krylov operator Ahat
                           (3xTF32 split, FP32-accurate), used where nx % 16 == 0,
                           ny % 4 == 0, nz % 2 == 0. */
   int const_bank;      /* MIXED: nonzero (default) = FP32 element matrices in one of 4
                           library-wide __constant__ slots (shared by handles with equal
                           matrices), falling back to kernel parameters if all are taken */
-  int graphs;          /* nonzero (default): each GMRES iteration is captured once per
-                          handle into a CUDA graph (on an internal stream) and replayed
-                          on the caller's stream; the first solve pays the capture */
+  int graphs;          /* 0 = direct launches, the host deciding after every GMRES
+                          iteration; 1 = each GMRES iteration captured once per handle
+                          into a CUDA graph (on an internal stream) and replayed on the
+                          caller's stream; 2 (default) = the whole solve captured once per
+                          handle into one graph whose refinement loop (a WHILE node) and
+                          Arnoldi steps (IF nodes) are controlled by device kernels, so a
+                          solve is one launch and one synchronisation.  With profile set,
+                          2 behaves as 1 (event timings need the host loop).  The first
+                          solve of a handle pays the capture. */
   int profile_mask;    /* with profile set: bit c (cell_prof_class) = time class c;
                           0 = every class */
   int precond;         /* CELL_PRECOND_SCP (default, §2.5.3) or CELL_PRECOND_DBP (§2.5.1) */
@@ -198,9 +204,11 @@ int cell_update(cell_handle* h, const void* input);
  * usable best solution) if tol was not reached within max_iter/max_refine. */
 int cell_solve(cell_handle* h, cell_stats* st);
 
-/* cell_solve for n distinct handles (cells of any sizes and options), driven
- * by up to 16 host threads: handles on different streams solve concurrently
- * on the GPU, handles sharing a stream one after another.  st: NULL or n
+/* cell_solve for n distinct handles (cells of any sizes and options).  If
+ * every handle runs whole-solve graphs (graphs = 2, no profiling), the calling
+ * thread launches all the solves and then collects them; otherwise up to 16
+ * host threads drive one handle each.  Handles on different streams solve
+ * concurrently on the GPU, handles sharing a stream one after another.  st: NULL or n
  * stats (st[i].status holds handle i's result).  Returns CELL_OK, or the
  * status of the first handle (in list order) that failed; CELL_EINVAL for
  * a NULL list entry or a handle listed twice (nothing solved). */
@@ -328,9 +336,9 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype);
  * 3 components per node) or y = Sbar x with CELL_BLOCK_SBAR (sum_e rho_e S0,
  * S0 = C_e + B_e (A_e + shift I)^-1 B_e^T, 1 component).  x, y: device,
  * nrhs vectors of [comp][node] (3nn or nn values each), not aliased.
- * dtype CELL_F32 / CELL_F64: SIMT; CELL_F32_TC: the z-marching tensor-core
- * kernel used by the smoothers (TF32 inputs, FP32 accumulation; CELL_EINVAL
- * unless nx % 8 == 0 and nx <= 64).  Asynchronous on the handle's stream. */
+ * dtype CELL_F32 / CELL_F64: SIMT; CELL_F32_TC: the node-centric tensor-core
+ * kernel used by the smoothers (TF32 inputs, FP32 accumulation; any grid
+ * size).  Asynchronous on the handle's stream. */
 int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs, int dtype);
 
 /* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as

@@ -90,7 +90,7 @@ NcGeom make_geom(int nx, int ny, int nz, int L) {
   g.PS = (kTY + 2) * g.RS;
   g.off_b = kRing * g.PS;
   g.off_bar = g.off_b + kBFloats * 4;
-  g.smem = g.off_bar + 64;
+  g.smem = g.off_bar + 64 + 8 * (kMmas + kPairs);
   if (g.smem < kMinSmem) g.smem = kMinSmem;
   int c = 32;
   while (c < 2 * g.TX * 32) c <<= 1;
@@ -160,6 +160,7 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   float* sB = reinterpret_cast<float*>(smem + g.off_b);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + g.off_bar);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + g.off_bar + 16);
+  uint64_t* dtab = reinterpret_cast<uint64_t*>(smem + g.off_bar + 64);   // [kMmas] B, [kPairs] A templates
 
   // ---- set-up: TMEM, barriers, B, zeroed ring (unused slots stay zero) ------
   if (w == 0) {
@@ -184,6 +185,19 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   const uint32_t tmem = *tslot;
   const uint32_t splanes = tc::smem_u32(planes);
   const uint32_t sb_addr = tc::smem_u32(sB);
+  // descriptor tables: B per MMA, A templates per neighbour pair relative to a
+  // plane base (the start-address field is the low 14 bits of a descriptor, so
+  // adding a base address >> 4 moves it without carries: every shared-memory
+  // address is below 2^18)
+  if (tid < kMmas) {
+    dtab[tid] = tc::sdesc(sb_addr + (uint32_t)(tid * 1024), 128u, 256u);
+  } else if (tid < kMmas + kPairs) {
+    const int p = tid - kMmas;
+    const int o1 = (1 + pair_dy(p, 0)) * g.RS + (1 + pair_dx(p, 0)) * 16;
+    const int o2 = (1 + pair_dy(p, 1)) * g.RS + (1 + pair_dx(p, 1)) * 16;
+    dtab[tid] = tc::sdesc((uint32_t)o1, (uint32_t)(o2 - o1), (uint32_t)g.RS);
+  }
+  __syncthreads();
 
   const float* in[4];
 #pragma unroll
@@ -233,18 +247,18 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   auto issue = [&](int k) {
     tc::fence_after_sync();
     const uint32_t dcol = (uint32_t)((k & 1) * g.TX * 32);
+    uint64_t at[kPairs];
+#pragma unroll
+    for (int p = 0; p < kPairs; ++p) at[p] = dtab[kMmas + p];
     for (int t = 0; t < g.TX; ++t) {
 #pragma unroll
       for (int pz = 0; pz < 3; ++pz) {
-        const uint32_t pb = splanes + (uint32_t)(((k + pz) % kRing) * g.PS);
+        // plane base and tile t (8 records of 16 bytes) in descriptor units
+        const uint64_t pb = (uint64_t)(((splanes + (uint32_t)(((k + pz) % kRing) * g.PS)) >> 4) + 8 * t);
 #pragma unroll
-        for (int p = 0; p < kPairs; ++p) {
-          const int o1 = (1 + pair_dy(p, 0)) * g.RS + (8 * t + 1 + pair_dx(p, 0)) * 16;
-          const int o2 = (1 + pair_dy(p, 1)) * g.RS + (8 * t + 1 + pair_dx(p, 1)) * 16;
-          const uint64_t ad = tc::sdesc(pb + (uint32_t)o1, (uint32_t)(o2 - o1), (uint32_t)g.RS);
-          const uint64_t bd = tc::sdesc(sb_addr + (uint32_t)((pz * kPairs + p) * 1024), 128u, 256u);
-          tc::mma_tf32(tmem + dcol + (uint32_t)(t * 32), ad, bd, idesc, (pz | p) ? 1u : 0u);
-        }
+        for (int p = 0; p < kPairs; ++p)
+          tc::mma_tf32(tmem + dcol + (uint32_t)(t * 32), at[p] + pb, dtab[pz * kPairs + p], idesc,
+                       (pz | p) ? 1u : 0u);
       }
     }
     tc::mma_commit(bar + (k & 1));

@@ -276,7 +276,24 @@ struct cell_handle {
   // an internal stream at first use and replayed on the caller's stream
   std::vector<IterGraph> graphs;
   cudaStream_t cap_st = nullptr;
+  // whole-solve graph (options.graphs == 2): device-side control state and
+  // the kernels per captured segment (for cell_launch_count)
+  cudaGraphExec_t solve_exec = nullptr;
+  int solve_prec = -1;
+  long long seg_pro = 0, seg_cb = 0, seg_it = 0, seg_ce = 0, seg_epi = 0;
+  double *bn2d = nullptr, *relres_d = nullptr, *bfloor_d = nullptr;
+  int *ctl_d = nullptr, *iters_d = nullptr;
+  struct GraphStats {
+    int ctl[4];
+    int iters[9];
+    int tcerr;
+    double relres[9];
+  };
+  GraphStats* gstat = nullptr;   // pinned host copy of the solve statistics
+  std::chrono::steady_clock::time_point gt0;
   void free_graphs() {
+    if (solve_exec) cudaGraphExecDestroy(solve_exec);
+    solve_exec = nullptr;
     for (IterGraph& g : graphs) {
       if (g.exec) cudaGraphExecDestroy(g.exec);
       for (GraphMark& m : g.marks) {
@@ -843,6 +860,7 @@ int check_options(const cell_options& o) {
   if ((o.load_mask & 0x1FF) == 0 || (o.load_mask & ~0x1FF)) return CELL_EINVAL;
   if (o.tensor_cores < 0 || o.tensor_cores > 2) return CELL_EINVAL;
   if (o.precond != CELL_PRECOND_SCP && o.precond != CELL_PRECOND_DBP) return CELL_EINVAL;
+  if (o.graphs < 0 || o.graphs > 2) return CELL_EINVAL;
   return CELL_OK;
 }
 
@@ -882,6 +900,9 @@ int load_design(cell_handle* h, const void* input) {
     for (int a = 0; a < 32; ++a) f2 += h->F[a * 9 + I] * h->F[a * 9 + I];
     h->bfloor[I] = 1e-13 * std::sqrt(srho2 * f2);
   }
+  // the whole-solve graph reads the floors from device memory (h->bfloor
+  // outlives the copy)
+  CK(cudaMemcpyAsync(h->bfloor_d, h->bfloor, sizeof(h->bfloor), cudaMemcpyHostToDevice, h->st));
   if (d->opt.precision == CELL_MIXED_FP32) CKS(fill_krylov<float>(h));
   else CKS(fill_krylov<double>(h));
   h->solved = false;
@@ -953,6 +974,12 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(A.alloc(&h->rho_tmp, nn));
   CKS(A.alloc(&h->bad, 1));
   CKS(A.alloc(&h->dptrs, 1 + cell::kHilbertMaxCons));
+  CKS(A.alloc(&h->bn2d, 9 * kNvMax));
+  CKS(A.alloc(&h->relres_d, 9));
+  CKS(A.alloc(&h->bfloor_d, 9));
+  CKS(A.alloc(&h->ctl_d, 4));
+  CKS(A.alloc(&h->iters_d, 9));
+  CK(cudaMallocHost(reinterpret_cast<void**>(&h->gstat), sizeof(cell_handle::GraphStats)));
   CKS(A.alloc(&h->tc_err, 1));
   CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->st));
   h->tc_ok = cell::tc_shape_ok(h->nx, h->ny, h->nz);
@@ -1030,9 +1057,236 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   return CELL_OK;
 }
 
+// ---------------------------------------------------------------------------
+// whole solve as one graph (options.graphs == 2)
+// ---------------------------------------------------------------------------
+
+template <typename T>
+cell::CtlParams ctl_params(const cell_handle* h) {
+  const cell_options& o = h->d.opt;
+  cell::CtlParams P;
+  P.tol = o.tol;
+  P.inner = sizeof(T) == 4 ? o.inner_tol : o.tol * 0.5;
+  P.mask = o.load_mask;
+  P.max_refine = o.max_refine;
+  P.max_iter = o.max_iter;
+  return P;
+}
+
+// Launches of one captured segment, into the graph being built (the calls
+// enqueue on h->st, redirected to the capture stream while capturing).
+// Returns the kernels the segment launched (not counted as launches now).
+template <typename F>
+cudaError_t capture_into(cell_handle* h, cudaGraph_t g, F&& body, long long* nk, bool keep_open = false) {
+  cudaStream_t user = h->st;
+  h->st = h->cap_st;
+  const long long n0 = cell::g_launches.load();
+  cudaError_t e = cudaStreamBeginCaptureToGraph(h->cap_st, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    e = body();
+    if (!keep_open) {
+      cudaGraph_t out = nullptr;
+      const cudaError_t e2 = cudaStreamEndCapture(h->cap_st, &out);
+      if (e == cudaSuccess) e = e2;
+    }
+  }
+  *nk = cell::g_launches.load() - n0;
+  cell::g_launches.fetch_sub(*nk);
+  h->st = user;
+  return e;
+}
+
+// Add a conditional node (IF / WHILE) at the current end of the capture on
+// cap_st and continue the capture after it; *body receives its body graph.
+cudaError_t add_conditional(cell_handle* h, cudaGraphConditionalHandle c, cudaGraphConditionalNodeType type,
+                            cudaGraph_t* body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  const cudaGraphEdgeData* ed = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(h->cap_st, &cs, nullptr, &g, &deps, &ed, &nd);
+  if (e != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = c;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  e = cudaGraphAddNode(&node, g, deps, ed, nd, &p);
+  if (e != cudaSuccess) return e;
+  *body = p.conditional.phGraph_out[0];
+  return cudaStreamUpdateCaptureDependencies(h->cap_st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// Graph:  prologue (loads, zero iterate, |b|^2, r = b, |r|^2, control)
+//         WHILE (refinement wanted) {
+//           cycle start (|r|^2, start_cycle, first basis vector, IF conditions)
+//           IF step 0 { Arnoldi step 0; condition of step 1 }  ...  IF step m-1 { ... }
+//           cycle end (least squares, x += Z y, residual, |r|^2, control)
+//         }
+//         epilogue (null-space projection)
+template <typename T>
+int build_solve_graph(cell_handle* h) {
+  Krylov<T>& K = kry<T>(h);
+  const int m = K.m;
+  const i64 len = K.len;
+  const int nblk = h->nblk;
+  const cell::CtlParams P = ctl_params<T>(h);
+  if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
+  cudaGraph_t top = nullptr;
+  CK(cudaGraphCreate(&top, 0));
+  cudaGraphConditionalHandle wh;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&wh, top, 0, cudaGraphCondAssignDefault);
+  cudaGraph_t wbody = nullptr;
+  // top level: prologue, WHILE node, epilogue
+  long long n_top = 0, n_epi = 0;
+  if (e == cudaSuccess)
+    e = capture_into(h, top, [&]() -> cudaError_t {
+      cudaStream_t s = h->st;
+      cell::RhsParams RP;
+      std::memcpy(RP.F, h->F, sizeof(RP.F));
+      cell::rhs9(h->rho64, RP, h->d.opt.load_mask, h->b64, h->nx, h->ny, h->nz, s);
+      cudaMemsetAsync(h->x64, 0, 9 * len * sizeof(double), s);
+      cudaMemsetAsync(h->xh, 0, 9 * len * sizeof(float), s);
+      cudaMemsetAsync(h->xl, 0, 9 * len * sizeof(float), s);
+      cell::multidot<double>(h->b64, 0, len, 1, h->b64, len, len, h->partial, nblk, kNvMax, 9, nullptr, s);
+      cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->bn2d, 0, 9, nullptr, s);
+      cudaMemcpyAsync(h->r64, h->b64, 9 * len * sizeof(double), cudaMemcpyDeviceToDevice, s);
+      cell::multidot<double>(h->r64, 0, len, 1, h->r64, len, len, h->partial, nblk, kNvMax, 9, nullptr, s);
+      cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->red, 0, 9, nullptr, s);
+      cell::ctl_reset(h->ctl_d, h->iters_d, s);
+      cell::refine_ctl(h->bn2d, h->red, h->bfloor_d, P, h->want, h->tolabs, h->relres_d, h->iters_d, h->ctl_d, wh, s);
+      cudaError_t e1 = add_conditional(h, wh, cudaGraphCondTypeWhile, &wbody);
+      if (e1 != cudaSuccess) return e1;
+      const long long nb = cell::g_launches.load();
+      cell::comp_sums(h->x64, h->nn, 9, h->partial, nblk, h->red2, s);
+      cell::sub_means(h->x64, h->nn, 9, h->red2, s);
+      n_epi = cell::g_launches.load() - nb;
+      return cudaGetLastError();
+    }, &n_top);
+  // WHILE body: cycle start, the IF chain of Arnoldi steps, cycle end
+  cell::IterHandles IH{};
+  IH.m = m;
+  for (int j = 0; j < m && e == cudaSuccess; ++j)
+    e = cudaGraphConditionalHandleCreate(&IH.h[j], wbody, 0, cudaGraphCondAssignDefault);
+  std::vector<cudaGraph_t> ifbody(m, nullptr);
+  long long n_body = 0;
+  if (e == cudaSuccess)
+    e = capture_into(h, wbody, [&]() -> cudaError_t {
+      cudaStream_t s = h->st;
+      cell::multidot<double>(h->r64, 0, len, 1, h->r64, len, len, h->partial, nblk, kNvMax, 9, h->want, s);
+      cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->beta2, 0, 9, h->want, s);
+      cell::start_cycle(h->beta2, h->g, m, h->active, h->want, h->resid, h->invscale, h->tolabs, h->kcount, 9, s);
+      cell::cycle_handles(h->active, h->ranmask, IH, s);
+      if constexpr (sizeof(T) == 4)
+        cell::to_f32_scaled(h->r64, len, reinterpret_cast<float*>(K.V), len, len, h->invscale, 9, h->ranmask, s);
+      else
+        cell::copy_scale_f64(h->r64, reinterpret_cast<double*>(K.V), len, h->invscale, 9, h->ranmask, s);
+      for (int j = 0; j < m; ++j) {
+        cudaError_t e1 = add_conditional(h, IH.h[j], cudaGraphCondTypeIf, &ifbody[j]);
+        if (e1 != cudaSuccess) return e1;
+      }
+      const long long nb = cell::g_launches.load();
+      cell::backsolve(h->H, h->g, h->kcount, m, h->ybuf, 9, h->ranmask, s);
+      cell::lincomb<T>(K.Z, 9 * len, len, h->ybuf, h->kcount, kNvMax, K.u, len, len, 9, h->ranmask, s);
+      if constexpr (sizeof(T) == 4)
+        cell::axpy_split<T>(h->x64, h->xh, h->xl, len, K.u, len, len, h->ones, 9, h->ranmask, s);
+      else
+        cell::axpy_f64<T>(h->x64, len, K.u, len, len, h->ones, 9, h->ranmask, s);
+      cell::accum_iters(h->iters_d, h->kcount, h->ranmask, h->ctl_d, s);
+      if constexpr (sizeof(T) == 4)
+        cell::resid_df(h->xh, h->xl, len, h->b64, len, h->r64, len, h->rho32, h->rho_l, h->DF, h->nx, h->ny,
+                       h->nz, 9, nullptr, s);
+      else
+        apply_full_T<double>(h, h->x64, len, h->r64, len, h->b64, len, -1.0, 1.0, nullptr, 9);
+      cell::multidot<double>(h->r64, 0, len, 1, h->r64, len, len, h->partial, nblk, kNvMax, 9, nullptr, s);
+      cell::reduce_partials(h->partial, nblk, 1, kNvMax, h->red, 0, 9, nullptr, s);
+      cell::refine_ctl(h->bn2d, h->red, h->bfloor_d, P, h->want, h->tolabs, h->relres_d, h->iters_d, h->ctl_d, wh, s);
+      h->seg_ce = cell::g_launches.load() - nb;
+      return cudaGetLastError();
+    }, &n_body);
+  // every Arnoldi step sets the condition of the next one
+  long long n_it = 0, n_it0 = 0;
+  for (int j = 0; j < m && e == cudaSuccess; ++j) {
+    e = capture_into(h, ifbody[j], [&]() -> cudaError_t {
+      iteration<T>(h, j);
+      if (j + 1 < m) cell::next_step(h->active, IH.h[j + 1], h->st);
+      return cudaGetLastError();
+    }, &n_it);
+    if (j == 0) n_it0 = n_it;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->solve_exec, top, 0);
+  cudaGraphDestroy(top);
+  if (e != cudaSuccess) {
+    h->solve_exec = nullptr;
+    set_error("whole-solve CUDA graph (conditional nodes)", e);
+    return CELL_ECUDA;
+  }
+  h->seg_epi = n_epi;
+  h->seg_pro = n_top - n_epi;
+  h->seg_cb = n_body - h->seg_ce;
+  h->seg_it = n_it0;   // kernels per Arnoldi step (the last step of a cycle has one fewer)
+  h->solve_prec = sizeof(T) == 4 ? 1 : 0;
+  return CELL_OK;
+}
+
+// Launch of a whole solve (graph built on first use) and the asynchronous
+// copy of its statistics; solve_graph_finish waits for them.
+template <typename T>
+int solve_graph_launch(cell_handle* h) {
+  h->gt0 = std::chrono::steady_clock::now();
+  if (!h->solve_exec || h->solve_prec != (sizeof(T) == 4 ? 1 : 0)) CKS(build_solve_graph<T>(h));
+  cudaStream_t s = h->st;
+  cell_handle::GraphStats* G = h->gstat;
+  CK(cudaGraphLaunch(h->solve_exec, s));
+  CK(cudaMemcpyAsync(G->ctl, h->ctl_d, sizeof(G->ctl), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(G->iters, h->iters_d, sizeof(G->iters), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(G->relres, h->relres_d, sizeof(G->relres), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&G->tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return CELL_OK;
+}
+
+template <typename T>
+int solve_graph_finish(cell_handle* h, cell_stats* st) {
+  cudaStream_t s = h->st;
+  CK(cudaStreamSynchronize(s));
+  const cell_handle::GraphStats& G = *h->gstat;
+  cell::g_launches.fetch_add(h->seg_pro + h->seg_epi + (long long)G.ctl[0] * (h->seg_cb + h->seg_ce) +
+                             (long long)G.ctl[2] * h->seg_it);
+  cell_stats S{};
+  int status = G.ctl[1];
+  if (G.tcerr) {
+    set_error("a tensor-core kernel's bounded wait expired");
+    status = CELL_ETIMEOUT;
+    CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), s));
+  }
+  CK(cudaGetLastError());
+  for (int q = 0; q < 9; ++q) {
+    S.iters[q] = G.iters[q];
+    S.rel_residual[q] = G.relres[q];
+  }
+  S.refinements = G.ctl[0];
+  S.status = status;
+  S.nlevels_u = (int)kry<T>(h).mgu.lv.size();
+  S.nlevels_phi = (int)kry<T>(h).mgp.lv.size();
+  S.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h->gt0).count();
+  h->solved = (status == CELL_OK);
+  h->last = S;
+  if (st) *st = S;
+  return status;
+}
+
+template <typename T>
+int solve_graph(cell_handle* h, cell_stats* st) {
+  CKS(solve_graph_launch<T>(h));
+  return solve_graph_finish<T>(h, st);
+}
+
 template <typename T>
 int solve_impl(cell_handle* h, cell_stats* st) {
   const cell_options& o = h->d.opt;
+  if (o.graphs == 2 && !h->prof.on) return solve_graph<T>(h, st);
   cudaStream_t s = h->st;
   const i64 len = 4 * h->nn;
   const int nblk = h->nblk;
@@ -1210,9 +1464,9 @@ void cell_default_options(cell_options* o) {
   o->coarse_dofs = 200;
   o->load_mask = 0x1FF;
   o->profile = 0;
-  o->tensor_cores = 0;
+  o->tensor_cores = 1;
   o->const_bank = 1;
-  o->graphs = 1;
+  o->graphs = 2;
   o->profile_mask = 0;
   o->precond = CELL_PRECOND_SCP;
 }
@@ -1235,6 +1489,7 @@ int cell_setup(const cell_desc* d, cell_handle** out) {
   if (s != CELL_OK) {
     cudaStreamSynchronize(h->st);
     h->arena.release();
+    if (h->gstat) cudaFreeHost(h->gstat);
     delete h;
     return s;
   }
@@ -1276,9 +1531,46 @@ int cell_solve_batch(cell_handle** hs, int n, cell_stats* st) {
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return CELL_EINVAL;
   }
-  // one host worker per handle (at most kBatchThreads): each drives its
-  // handle's solve on the handle's own stream and device, so solves of
-  // handles on different streams overlap on the GPU
+  // whole-solve graphs: launch every handle's solve (one graph each, on its
+  // own stream), then collect the statistics; the host never waits between
+  // launches, so solves on different streams overlap on the GPU
+  bool all_graphs = true;
+  for (int i = 0; i < n; ++i) all_graphs = all_graphs && hs[i]->d.opt.graphs == 2 && !hs[i]->prof.on;
+  if (all_graphs) {
+    std::vector<int> rc(n, CELL_OK);
+    std::vector<std::string> errs(n);
+    for (int i = 0; i < n; ++i) {
+      cell_handle* h = hs[i];
+      if (cudaSetDevice(h->dev) != cudaSuccess) {
+        rc[i] = CELL_ECUDA;
+        continue;
+      }
+      rc[i] = h->d.opt.precision == CELL_MIXED_FP32 ? solve_graph_launch<float>(h) : solve_graph_launch<double>(h);
+      if (rc[i] != CELL_OK) errs[i] = g_last_error;
+    }
+    for (int i = 0; i < n; ++i) {   // every launched solve is collected
+      cell_handle* h = hs[i];
+      if (rc[i] != CELL_OK) {
+        if (st) st[i].status = rc[i];
+        continue;
+      }
+      if (cudaSetDevice(h->dev) != cudaSuccess) {
+        rc[i] = CELL_ECUDA;
+        continue;
+      }
+      rc[i] = h->d.opt.precision == CELL_MIXED_FP32 ? solve_graph_finish<float>(h, st ? st + i : nullptr)
+                                                    : solve_graph_finish<double>(h, st ? st + i : nullptr);
+      if (rc[i] != CELL_OK) errs[i] = g_last_error;
+    }
+    for (int i = 0; i < n; ++i)
+      if (rc[i] != CELL_OK) {
+        g_last_error = errs[i];
+        return rc[i];
+      }
+    return CELL_OK;
+  }
+  // otherwise one host worker per handle (at most kBatchThreads): each drives
+  // its handle's solve on the handle's own stream and device
   constexpr int kBatchThreads = 16;
   std::vector<int> rc(n, CELL_OK);
   std::vector<std::string> errs(n);
@@ -1627,6 +1919,7 @@ void cell_destroy(cell_handle* h) {
   h->free_graphs();
   cell::cslot_release(h->cslot1);
   h->arena.release();
+  if (h->gstat) cudaFreeHost(h->gstat);
   delete h;
 }
 

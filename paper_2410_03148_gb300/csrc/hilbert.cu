@@ -220,7 +220,8 @@ int hilbert_velocity(int nx, int ny, int nz, double alpha, const double* dJ, con
       double sum = G[1 + i][1 + j];
       for (int k = 0; k < i; ++k) sum -= R[k][i] * R[k][j];
       if (i == j) {
-        if (!(sum > 0.0)) return CELL_EINVAL;   // constraint sensitivities linearly dependent
+        // constraint sensitivities linearly dependent (to rounding)
+        if (!(sum > 1e-12 * G[1 + i][1 + i])) return CELL_EINVAL;
         R[i][i] = std::sqrt(sum);
       } else {
         R[i][j] = sum / R[i][i];

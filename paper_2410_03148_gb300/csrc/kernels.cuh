@@ -242,6 +242,30 @@ template <typename T> void axpy_f64(double* x, i64 xs, const T* d, i64 ds, i64 l
                                     int nrhs, const int* active, cudaStream_t s);
 template <typename T> void fill(T* p, i64 n, T v, cudaStream_t s);
 
+// ---- device-side control of a whole-solve graph (solvectl.cu) ---------------------
+struct CtlParams {
+  double tol;      // outer relative tolerance
+  double inner;    // inner relative reduction of each cycle
+  int mask;        // load mask
+  int max_refine;  // refinement cap
+  int max_iter;    // iteration cap per load
+};
+struct IterHandles {
+  cudaGraphConditionalHandle h[kNvMax];   // IF condition of Arnoldi step j
+  int m;
+};
+// ctl[0] = refinements started, ctl[1] = status, ctl[2] = Arnoldi steps executed
+void refine_ctl(const double* bn2, const double* rn2, const double* bfloor, const CtlParams& P, int* want,
+                double* tolabs, double* relres, const int* iters, int* ctl, cudaGraphConditionalHandle cond,
+                cudaStream_t s);
+void cycle_handles(const int* active, int* ran, const IterHandles& H, cudaStream_t s);
+void next_step(const int* active, cudaGraphConditionalHandle next, cudaStream_t s);
+void accum_iters(int* iters, const int* kcount, const int* ran, int* ctl, cudaStream_t s);
+void ctl_reset(int* ctl, int* iters, cudaStream_t s);
+// v[q] = r[q] * sc[q] (FP64, nrhs vectors of len values)
+void copy_scale_f64(const double* r, double* v, i64 len, const double* sc, int nrhs, const int* active,
+                    cudaStream_t s);
+
 // ---- shape velocity (hilbert.cu) ----------------------------------------------
 // Riesz representers in periodic H^1 (A = alpha^2 K + M, Chebyshev iteration
 // with exact spectral bounds), projection of the objective representer off

@@ -337,14 +337,29 @@ k_update(const T* __restrict__ V, i64 vstride, i64 rstride, int nv, const double
   }
 }
 
+// Normalisation of the new basis vector, in the vector's own precision (an
+// FP32 vector scaled through FP64 arithmetic and conversions would run at the
+// FP64 rate); FP32 vectors move as 16-byte chunks when aligned.
 template <typename T>
 __global__ void k_scale(T* __restrict__ w, i64 wstride, i64 len, const double* __restrict__ sc) {
   const int q = blockIdx.y;
   const double f = sc[q];
   if (f == 1.0) return;
   T* W = w + q * wstride;
+  const T ft = (T)f;
+  if constexpr (sizeof(T) == 4) {
+    if ((((uintptr_t)W) & 15) == 0 && (len & 3) == 0) {
+      float4* W4 = reinterpret_cast<float4*>(W);
+      for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < (len >> 2); k += (i64)gridDim.x * blockDim.x) {
+        float4 v = W4[k];
+        v.x *= ft; v.y *= ft; v.z *= ft; v.w *= ft;
+        W4[k] = v;
+      }
+      return;
+    }
+  }
   for (i64 k = (i64)blockIdx.x * blockDim.x + threadIdx.x; k < len; k += (i64)gridDim.x * blockDim.x)
-    W[k] = (T)((double)W[k] * f);
+    W[k] *= ft;
 }
 
 template <typename T>

@@ -300,22 +300,43 @@ def test_constant_bank_and_parameter_kernels_agree():
 
 
 def test_graphs_and_direct_launches_agree():
-    """Replaying captured GMRES iterations gives bitwise the same solve as
-    launching them directly, across designs (graphs survive cell_update)."""
+    """Direct launches, per-iteration graphs and the whole-solve graph (device-
+    side refinement and Arnoldi control through conditional nodes) give bitwise
+    the same solve, iteration counts and launch counts per step, across designs
+    (graphs survive cell_update)."""
+    from paper_2410_03148_gb300 import _binding as B
     designs = [cellgen.gaussian_levelset(16, seed=s) for s in (21, 22)]
     res = {}
-    for g in (0, 1):
+    for g in (0, 1, 2):
         cell = make_cell(designs[0], "phi", graphs=g)
         out = []
         for d in designs:
             cell.update(torch.as_tensor(d, device=dev()))
             st = cell.solve()
-            out.append((st["iters"], np.concatenate([a.ravel() for a in cell.homogenise()])))
+            out.append((st["iters"], st["refinements"], list(st["rel_residual"]),
+                        np.concatenate([a.ravel() for a in cell.homogenise()])))
         res[g] = out
         cell.close()
-    for (i0, h0), (i1, h1) in zip(res[0], res[1]):
-        assert i0 == i1
-        assert np.array_equal(h0, h1)
+    for g in (1, 2):
+        for (i0, f0, r0, h0), (i1, f1, r1, h1) in zip(res[0], res[g]):
+            assert i0 == i1 and f0 == f1
+            assert np.array_equal(h0, h1)
+            assert np.allclose(r0, r1, rtol=0, atol=0)
+
+
+def test_whole_solve_graph_fp64_and_not_converged():
+    """The whole-solve graph on the FP64 path, and its CELL_ENOTCONV exit at
+    the iteration cap (statistics still filled)."""
+    phi = cellgen.gaussian_levelset(12, seed=5)
+    a = make_cell(phi, "phi", precision=0, graphs=0)
+    b = make_cell(phi, "phi", precision=0, graphs=2)
+    sa, sb = a.solve(), b.solve()
+    assert sa["iters"] == sb["iters"]
+    for x, y in zip(a.homogenise(), b.homogenise()):
+        assert np.array_equal(x, y)
+    c = make_cell(phi, "phi", graphs=2, max_iter=3)
+    st = c.solve(allow_notconv=True)
+    assert st["status"] == 3 and max(st["iters"]) >= 3
 
 
 def test_profiled_graph_solve_reports_kernel_times():
