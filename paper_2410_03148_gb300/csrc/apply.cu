@@ -785,8 +785,9 @@ template <typename T, int NC>
 void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
   const long long nn = (long long)a.nx * a.ny * a.nz;
   // three loads per thread on large levels: all nine per thread reads the
-  // stencil once per apply but chains 27 rounds of 36 dependent loads per
-  // thread, and measured 1.4x slower (64^3 level: 234 against 170 us)
+  // stencil once per apply but chains 27 rounds of 36 loads per thread, and
+  // the coarse levels of a 128^3 step measured slower with it (68.8 against
+  // 61.8 ms per step)
   if (nn > 16384) launch_st<T, NC, 3>(a, mode, nrhs, s);
   else if (nn > kSplitMaxNodes) launch_st<T, NC, 1>(a, mode, nrhs, s);
   else launch_st_split<T, NC>(a, mode, nrhs, s);
