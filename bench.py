@@ -636,6 +636,7 @@ def main():
             "clocks": clocks,
             "detail": {"wall_s": wall, "step_ms": step_ms, "gmres_iters_max": iters,
                        "refinements": [s["refinements"] for s in stats],
+                       "tc_tiles_autotuned": {"elastic": stats[0]["tc_tiles"][0], "schur": stats[0]["tc_tiles"][1]},
                        "class_ms_per_step": share_ms, "class_share": class_share,
                        "class_source": "separate fully profiled pass over the same designs "
                                        "(untimed); the timed region times only the roofline kernel"},

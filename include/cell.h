@@ -122,6 +122,11 @@ typedef struct cell_options {
   int profile_mask;    /* with profile set: bit c (cell_prof_class) = time class c;
                           0 = every class */
   int precond;         /* CELL_PRECOND_SCP (default, §2.5.3) or CELL_PRECOND_DBP (§2.5.1) */
+  int autotune;        /* MIXED with tensor_cores >= 1: nonzero (default) = at cell_setup, time
+                          the tensor-core smoothers' CTA tiles (x width 8/16/32 nodes, z-chunk
+                          length) on this GPU and grid and keep the fastest per block (cell_stats
+                          reports them); every tile gives bitwise the same result.  0 = widest
+                          tile and a wave-count heuristic. */
 } cell_options;
 
 typedef enum cell_precond {
@@ -170,6 +175,10 @@ typedef struct cell_stats {
   int class_count[CELL_PROF_CLASSES];   /* profile: launches timed per class */
   long long class_units[CELL_PROF_CLASSES]; /* profile: sum over timed launches of the
                                            number of loads each launch processed */
+  int tc_tile_xt[2], tc_tile_L[2];  /* tensor-core smoother tile in use per block ([0] elastic
+                                       A, [1] Schur Sbar): x width in nodes and z-chunk length;
+                                       0 = not tuned (default tile or SIMT path) */
+  double tc_tile_us[2];             /* the tuned tile's time per 9-load Chebyshev launch, us */
 } cell_stats;
 
 typedef struct cell_handle cell_handle;
@@ -340,6 +349,19 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype);
  * kernel used by the smoothers (TF32 inputs, FP32 accumulation; any grid
  * size).  Asynchronous on the handle's stream. */
 int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs, int dtype);
+
+/* Set the CTA tile of the tensor-core smoother of one block (cell_block) for
+ * the rest of the handle's life, replacing the one cell_setup tuned or chose:
+ * xt = nodes along x per CTA (8, 16 or 32, at most nx rounded up to a multiple
+ * of 8), L = z-planes per CTA chunk (>= 1; values above nz act as nz); xt = L
+ * = 0 restores the default tile.  Results do not depend on the tile (each
+ * node's tensor-core sequence and epilogue are the same); it changes launch
+ * geometry and speed only.  Takes effect for later launches; a solve graph
+ * captured before the call keeps the tile it was captured with.  Errors:
+ * CELL_EINVAL for a null handle, an unknown block, a tile outside those ranges,
+ * or a handle without the tensor-core path (FP64 precision, tensor_cores = 0
+ * or a grid it does not support). */
+int cell_set_tile(cell_handle* h, int block, int xt, int L);
 
 /* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as
  * FP64 cell vectors into the DEVICE buffer out (9*4*N values). */

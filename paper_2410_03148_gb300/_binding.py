@@ -28,7 +28,7 @@ EXPORTS = [
     "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_solve_batch", "cell_homogenise",
     "cell_sensitivity", "cell_sensitivity_phi", "cell_hj_step",
     "cell_dh", "cell_figure", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
-    "cell_element_matrices", "cell_homogenise_noalloc", "cell_energy_difference", "cell_hilbert_velocity", "cell_launch_count", "cell_destroy",
+    "cell_element_matrices", "cell_homogenise_noalloc", "cell_energy_difference", "cell_hilbert_velocity", "cell_set_tile", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
 ]
 
@@ -41,7 +41,7 @@ class cell_options(C.Structure):
         ("cheb_hi", C.c_double), ("schur_shift", C.c_double), ("coarse_dofs", C.c_int),
         ("load_mask", C.c_int), ("profile", C.c_int), ("tensor_cores", C.c_int),
         ("const_bank", C.c_int), ("graphs", C.c_int), ("profile_mask", C.c_int),
-        ("precond", C.c_int),
+        ("precond", C.c_int), ("autotune", C.c_int),
     ]
 
 
@@ -65,6 +65,7 @@ class cell_stats(C.Structure):
         ("solve_ms", C.c_double), ("class_ms", C.c_double * len(PROF_CLASSES)),
         ("class_count", C.c_int * len(PROF_CLASSES)),
         ("class_units", C.c_longlong * len(PROF_CLASSES)),
+        ("tc_tile_xt", C.c_int * 2), ("tc_tile_L", C.c_int * 2), ("tc_tile_us", C.c_double * 2),
     ]
 
 
@@ -106,6 +107,7 @@ def load(path: str = LIB_PATH):
     lib.cell_get_solution.argtypes = [P, P]
     lib.cell_apply.argtypes = [P, P, P, C.c_int, C.c_int]
     lib.cell_apply_block.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
+    lib.cell_set_tile.argtypes = [P, C.c_int, C.c_int, C.c_int]
     lib.cell_rhs.argtypes = [P, P]
     lib.cell_get_rho.argtypes = [P, P]
     lib.cell_element_matrices.argtypes = [C.POINTER(cell_desc), D, D]
@@ -296,6 +298,10 @@ def cell_apply(h, x_ptr: int, y_ptr: int, nrhs: int, dtype: int):
 def cell_apply_block(h, block: int, x_ptr: int, y_ptr: int, nrhs: int, dtype: int):
     _check("cell_apply_block",
            load().cell_apply_block(h, block, C.c_void_p(x_ptr), C.c_void_p(y_ptr), nrhs, dtype))
+
+
+def cell_set_tile(h, block: int, xt: int, L: int):
+    _check("cell_set_tile", load().cell_set_tile(h, block, xt, L))
 
 
 def cell_rhs(h, out_ptr: int):

@@ -29,6 +29,7 @@ def _stats_dict(status, st):
         "class_units": dict(zip(B.PROF_CLASSES, list(st.class_units))),
         "nlevels_u": st.nlevels_u,
         "nlevels_phi": st.nlevels_phi,
+        "tc_tiles": [{"xt": st.tc_tile_xt[k], "L": st.tc_tile_L[k], "us": st.tc_tile_us[k]} for k in range(2)],
     }
 
 
@@ -144,6 +145,12 @@ class Cell:
         blk = B.CELL_BLOCK_A if block == "A" else B.CELL_BLOCK_SBAR
         B.cell_apply_block(self._h, blk, x.data_ptr(), y.data_ptr(), x.shape[0], dt)
         return y
+
+    def set_tile(self, block: str, xt: int = 0, L: int = 0) -> None:
+        """Fix the tensor-core smoother tile of block "A" or "Sbar" (xt nodes
+        along x: 8, 16 or 32; L z-planes per chunk); 0, 0 = the default tile."""
+        blk = B.CELL_BLOCK_A if block == "A" else B.CELL_BLOCK_SBAR
+        B.cell_set_tile(self._h, blk, xt, L)
 
     def rhs(self) -> torch.Tensor:
         out = torch.empty((9, 4) + self.shape, dtype=torch.float64, device=self.device)

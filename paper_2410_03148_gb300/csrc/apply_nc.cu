@@ -75,12 +75,15 @@ struct NcGeom {
   int tcols;           // TMEM columns allocated (power of two)
 };
 
-NcGeom make_geom(int nx, int ny, int nz, int L) {
+// Widest tile for a grid: 32 nodes, or nx rounded up to a multiple of 8.
+int max_xt(int nx) { return nx >= 32 ? 32 : ((nx + 7) / 8) * 8; }
+
+NcGeom make_geom(int nx, int ny, int nz, int L, int XT) {
   NcGeom g{};
   g.nx = nx;
   g.ny = ny;
   g.nz = nz;
-  g.XT = nx >= 32 ? 32 : ((nx + 7) / 8) * 8;
+  g.XT = XT;
   g.TX = g.XT / 8;
   g.gx = (nx + g.XT - 1) / g.XT;
   g.gy = (ny + kTY - 1) / kTY;
@@ -168,8 +171,8 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(bar, 1);
-    tc::mbar_init(bar + 1, 1);
+    tc::mbar_init(bar, (uint32_t)g.TX);       // one commit per M tile
+    tc::mbar_init(bar + 1, (uint32_t)g.TX);
   }
   for (int i = tid; i < kBFloats; i += kThreads) sB[i] = Btab[i];
   {
@@ -242,24 +245,21 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
     }
   };
 
-  // MMAs of output plane k (planes k, k + 1, k + 2 of the ring) into TMEM buffer k % 2
+  // MMAs of M tile t of output plane k (planes k, k + 1, k + 2 of the ring)
+  // into TMEM buffer k % 2.  Lane 0 of warp t issues tile t: the tiles'
+  // accumulators are disjoint, so the issue work is spread over TX warps, and
+  // each issuer's commit is one of the TX arrivals the plane's barrier expects.
   const uint32_t idesc = tc::idesc_tf32(128, 32);
-  auto issue = [&](int k) {
+  auto issue = [&](int k, int t) {
     tc::fence_after_sync();
-    const uint32_t dcol = (uint32_t)((k & 1) * g.TX * 32);
-    uint64_t at[kPairs];
+    const uint32_t dcol = (uint32_t)((k & 1) * g.TX * 32 + t * 32);
 #pragma unroll
-    for (int p = 0; p < kPairs; ++p) at[p] = dtab[kMmas + p];
-    for (int t = 0; t < g.TX; ++t) {
+    for (int pz = 0; pz < 3; ++pz) {
+      // plane base and tile t (8 records of 16 bytes) in descriptor units
+      const uint64_t pb = (uint64_t)(((splanes + (uint32_t)(((k + pz) % kRing) * g.PS)) >> 4) + 8 * t);
 #pragma unroll
-      for (int pz = 0; pz < 3; ++pz) {
-        // plane base and tile t (8 records of 16 bytes) in descriptor units
-        const uint64_t pb = (uint64_t)(((splanes + (uint32_t)(((k + pz) % kRing) * g.PS)) >> 4) + 8 * t);
-#pragma unroll
-        for (int p = 0; p < kPairs; ++p)
-          tc::mma_tf32(tmem + dcol + (uint32_t)(t * 32), at[p] + pb, dtab[pz * kPairs + p], idesc,
-                       (pz | p) ? 1u : 0u);
-      }
+      for (int p = 0; p < kPairs; ++p)
+        tc::mma_tf32(tmem + dcol, dtab[kMmas + p] + pb, dtab[pz * kPairs + p], idesc, (pz | p) ? 1u : 0u);
     }
     tc::mma_commit(bar + (k & 1));
   };
@@ -277,14 +277,18 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   const int ym = gy == 0 ? ny - 1 : gy - 1;
   constexpr int kTilesPerWarp = 2;   // TX <= 4 tiles, two warps per lane quarter
 
-  // Epilogue of output plane k: operands are prefetched, then the bounded wait
-  // for the plane's MMAs, then TMEM -> registers -> rho-weighted sum -> output.
-  auto epilogue = [&](int k) -> bool {
+  // Epilogue of output plane k in two parts.  prefetch(k) loads the node-wise
+  // operands and the 8 rho values of each of the thread's nodes into registers
+  // one step ahead (they are inputs the MMAs do not depend on, and the y and sol
+  // entries a thread reads are the ones it alone writes); finish(k) waits
+  // (bounded) for the plane's MMAs and runs TMEM -> registers -> rho-weighted
+  // sum -> output.
+  float rho[kTilesPerWarp][8];
+  float e0[kTilesPerWarp][NS], e1[kTilesPerWarp][NS], e2[kTilesPerWarp][NS];
+  bool valid[kTilesPerWarp];
+  auto prefetch = [&](int k) {
     const int gz = z0 + k;
     const int zm = gz == 0 ? nz - 1 : gz - 1;
-    float rho[kTilesPerWarp][8];
-    float e0[kTilesPerWarp][NS], e1[kTilesPerWarp][NS], e2[kTilesPerWarp][NS];
-    bool valid[kTilesPerWarp];
 #pragma unroll
     for (int j = 0; j < kTilesPerWarp; ++j) {
       const int t = (w >> 2) + 2 * j;
@@ -316,9 +320,11 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
         }
       }
     }
-    const bool ok = tc::mbar_wait_bounded(bar + (k & 1), (uint32_t)((k >> 1) & 1), kWaitLimit);
-    if (__syncthreads_or(!ok)) return false;   // uniform: every thread gives up together
+  };
+  auto finish = [&](int k) -> bool {
+    if (!tc::mbar_wait_bounded(bar + (k & 1), (uint32_t)((k >> 1) & 1), kWaitLimit)) return false;
     tc::fence_after_sync();
+    const int gz = z0 + k;
     const unsigned char* pl = planes + ((k + 1) % kRing) * g.PS;   // the output plane's records
 #pragma unroll
     for (int j = 0; j < kTilesPerWarp; ++j) {
@@ -346,12 +352,16 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   };
 
   // ---- pipeline --------------------------------------------------------------
-  // Ring argument: plane p_new = k + 2 + kAhead is staged at step k into the
-  // slot of p_old = p_new - kRing.  p_old is read by the MMAs of output planes
-  // up to p_old (completion awaited by the epilogue at step p_old + 1) and by
-  // the epilogue of output plane p_old - 1 (at step p_old); kRing = kAhead + 4
-  // puts both before step k.  TMEM buffer k % 2 is rewritten at step k + 2,
-  // after the epilogue of plane k (step k + 1) and a block barrier.
+  // One block barrier per step.  Ring argument: plane p_new = k + 2 + kAhead is
+  // staged at step k into the slot of p_old = p_new - kRing = k - 2.  p_old is
+  // read by the MMAs of output planes up to k - 2, whose completion this thread
+  // awaited in the epilogue of plane k - 2 (step k - 1), and by the epilogue of
+  // output plane k - 3 (step k - 2), which every thread finished before the
+  // barrier of step k - 1.  TMEM buffer k % 2 is rewritten by the MMAs issued
+  // at step k + 2, after the barrier that follows every thread's epilogue of
+  // plane k (step k + 1).  A thread whose wait gives up skips its remaining
+  // epilogues but keeps taking the barriers.  The operands of plane k are
+  // loaded at the end of step k and used at step k + 1.
   for (int p = 0; p < 2 + kAhead; ++p) {
     stage_plane(p);
     cp_async_commit();
@@ -363,26 +373,23 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
     cp_async_commit();
     cp_async_wait<kAhead>();      // planes 0 .. k + 2 have landed
     tc::fence_async_smem();
-    __syncthreads();
-    if (tid == 0) issue(k);
-    ++issued;
-    if (k >= 1) {
-      if (!epilogue(k - 1)) {
-        aborted = true;
-        break;
-      }
-      ++waited;
-    }
     tc::fence_before_sync();
     __syncthreads();
+    if (l == 0 && w < g.TX) issue(k, w);
+    ++issued;
+    if (k >= 1 && !aborted) {
+      if (finish(k - 1)) ++waited;
+      else aborted = true;
+    }
+    prefetch(k);
   }
   if (!aborted) {
-    if (epilogue(L - 1)) ++waited;
+    if (finish(L - 1)) ++waited;
     else aborted = true;
   }
   cp_async_wait<0>();
   if (aborted) {
-    if (tid == 0) atomicAdd(err, 1);
+    atomicAdd(err, 1);
     // let every committed MMA group finish (bounded) before TMEM is released
     for (int k = waited; k < issued; ++k)
       if (!tc::mbar_wait_bounded(bar + (k & 1), (uint32_t)((k >> 1) & 1), kWaitLimit)) break;
@@ -414,8 +421,9 @@ int num_sms() {
   return g_nsm[dev];
 }
 
-// Planes per z chunk: the candidate with the smallest (waves x staged planes)
-// for two resident CTAs per SM (the z halo costs two planes per chunk).
+// Default tile: the widest XT, and the chunk length L with the smallest
+// (waves x staged planes) for two resident CTAs per SM (the z halo costs two
+// planes per chunk).
 int choose_chunk(int units, const NcGeom& g0) {
   const int slots = 2 * num_sms();
   const int cand[] = {4, 8, 16, 32, 64, 128, 256};
@@ -435,12 +443,19 @@ int choose_chunk(int units, const NcGeom& g0) {
   return best;
 }
 
+constexpr int units_of(int kind, int nrhs) { return kind == NK_UU ? nrhs : (nrhs + 3) / 4; }
+
+NcGeom geom_for(int kind, const ApplyArgs<float>& a, int nrhs, NcTile tile) {
+  const int xt = tile.xt ? tile.xt : max_xt(a.nx);
+  const int L = tile.L ? (tile.L < a.nz ? tile.L : a.nz)
+                       : choose_chunk(units_of(kind, nrhs), make_geom(a.nx, a.ny, a.nz, a.nz, xt));
+  return make_geom(a.nx, a.ny, a.nz, L, xt);
+}
+
 template <int KIND, int MODE>
-bool launch(const ApplyArgs<float>& a, const float* Btab, int nrhs, int* err, cudaStream_t s) {
-  constexpr int UPL = KIND == NK_UU ? 1 : 4;
-  const int units = (nrhs + UPL - 1) / UPL;
-  const NcGeom g0 = make_geom(a.nx, a.ny, a.nz, a.nz);
-  const NcGeom g = make_geom(a.nx, a.ny, a.nz, choose_chunk(units, g0));
+bool launch(const ApplyArgs<float>& a, const float* Btab, int nrhs, int* err, cudaStream_t s, NcTile tile) {
+  const int units = units_of(KIND, nrhs);
+  const NcGeom g = geom_for(KIND, a, nrhs, tile);
   if ((long long)g.zchunks * units > 65535 || g.gy > 65535) return false;
   const dim3 grid((unsigned)g.gx, (unsigned)g.gy, (unsigned)(g.zchunks * units));
   note_launch(), k_nc<KIND, MODE><<<grid, kThreads, g.smem, s>>>(a, Btab, g, nrhs, err);
@@ -455,11 +470,11 @@ void set_attr(int smem) {
 }  // namespace
 
 bool nc_shape_ok(int nx, int ny, int nz) {
-  return nx >= 2 && ny >= 2 && nz >= 2 && make_geom(nx, ny, nz, 1).smem <= 227 * 1024;
+  return nx >= 2 && ny >= 2 && nz >= 2 && make_geom(nx, ny, nz, 1, max_xt(nx)).smem <= 227 * 1024;
 }
 
 void nc_prepare() {
-  const int smem = make_geom(32, 16, 2, 1).smem;   // the widest tile
+  const int smem = make_geom(32, 16, 2, 1, 32).smem;   // the widest tile
   set_attr<NK_UU, AM_LINEAR>(smem);
   set_attr<NK_UU, AM_CHEB>(smem);
   set_attr<NK_UU, AM_CHEB_LAST>(smem);
@@ -509,21 +524,67 @@ void nc_build_b(int kind, const double* K0, const double* S0, float* out) {
 }
 
 bool apply_nc(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
-              cudaStream_t s) {
+              cudaStream_t s, NcTile tile) {
   if (kind == NK_UU) {
     switch (mode) {
-      case AM_LINEAR: return launch<NK_UU, AM_LINEAR>(a, Btab, nrhs, err, s);
-      case AM_CHEB: return launch<NK_UU, AM_CHEB>(a, Btab, nrhs, err, s);
-      case AM_CHEB_LAST: return launch<NK_UU, AM_CHEB_LAST>(a, Btab, nrhs, err, s);
-      default: return launch<NK_UU, AM_RESID_CHEB0>(a, Btab, nrhs, err, s);
+      case AM_LINEAR: return launch<NK_UU, AM_LINEAR>(a, Btab, nrhs, err, s, tile);
+      case AM_CHEB: return launch<NK_UU, AM_CHEB>(a, Btab, nrhs, err, s, tile);
+      case AM_CHEB_LAST: return launch<NK_UU, AM_CHEB_LAST>(a, Btab, nrhs, err, s, tile);
+      default: return launch<NK_UU, AM_RESID_CHEB0>(a, Btab, nrhs, err, s, tile);
     }
   }
   switch (mode) {
-    case AM_LINEAR: return launch<NK_SS4, AM_LINEAR>(a, Btab, nrhs, err, s);
-    case AM_CHEB: return launch<NK_SS4, AM_CHEB>(a, Btab, nrhs, err, s);
-    case AM_CHEB_LAST: return launch<NK_SS4, AM_CHEB_LAST>(a, Btab, nrhs, err, s);
-    default: return launch<NK_SS4, AM_RESID_CHEB0>(a, Btab, nrhs, err, s);
+    case AM_LINEAR: return launch<NK_SS4, AM_LINEAR>(a, Btab, nrhs, err, s, tile);
+    case AM_CHEB: return launch<NK_SS4, AM_CHEB>(a, Btab, nrhs, err, s, tile);
+    case AM_CHEB_LAST: return launch<NK_SS4, AM_CHEB_LAST>(a, Btab, nrhs, err, s, tile);
+    default: return launch<NK_SS4, AM_RESID_CHEB0>(a, Btab, nrhs, err, s, tile);
   }
+}
+
+// Tile autotuner.  Every (XT, L) candidate computes bitwise the same result
+// (a node's MMA sequence and epilogue do not depend on the tiling), so the
+// choice is free: each candidate is timed on the caller's buffers in the given
+// mode (one warm-up launch, then kTuneReps launches between CUDA events on the
+// stream) and the fastest kept.  Candidates: XT in {8, 16, 32} up to the grid's
+// widest tile, L in {4, 8, ..., 256} up to nz (and nz itself), within the
+// launch limits.  Returns the default tile if nothing could be timed.
+NcTile nc_autotune(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
+                   cudaStream_t s, float* best_us) {
+  constexpr int kTuneReps = 3;
+  NcTile best{0, 0};
+  float best_t = 3.0e38f;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    if (best_us) *best_us = 0.f;
+    return best;
+  }
+  const int xts[] = {8, 16, 32};
+  const int Ls[] = {4, 8, 16, 32, 64, 128, 256};
+  for (int xt : xts) {
+    if (xt > max_xt(a.nx)) break;
+    for (int i = 0; i <= 7; ++i) {
+      int L = i < 7 ? Ls[i] : a.nz;
+      if (i < 7 && L >= a.nz) continue;   // nz itself is the last candidate
+      const NcTile t{xt, L};
+      if (!apply_nc(kind, a, Btab, mode, nrhs, err, s, t)) continue;
+      cudaEventRecord(e0, s);
+      bool ok = true;
+      for (int r = 0; r < kTuneReps && ok; ++r) ok = apply_nc(kind, a, Btab, mode, nrhs, err, s, t);
+      cudaEventRecord(e1, s);
+      float ms = 0.f;
+      if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+        continue;
+      if (ms < best_t) {
+        best_t = ms;
+        best = t;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_us) *best_us = best.xt ? best_t * 1000.f / kTuneReps : 0.f;
+  return best;
 }
 
 }  // namespace cell

@@ -254,6 +254,8 @@ struct cell_handle {
   bool tc_ok = false;      // grid tiles into tensor-core bricks
   bool nc_ok = false;      // grid suits the node-centric tensor-core smoothers
   float* ncb = nullptr;    // their B operands: [NK_UU | NK_SS4][nc_table_floats()]
+  cell::NcTile nct[2] = {{0, 0}, {0, 0}};   // their CTA tiles (autotuned at set-up)
+  float nct_us[2] = {0.f, 0.f};
   cell::TcTables tct;      // tensor-core operand tables (device)
   int cslot1 = 0;          // constant-bank slot of the FP32 element matrices (+1)
   cell::DFMat DF;
@@ -311,6 +313,9 @@ namespace {
 
 template <typename T> Krylov<T>& kry(cell_handle* h);
 template <> Krylov<float>& kry<float>(cell_handle* h) { return h->kf; }
+
+int tune_tiles(cell_handle* h);
+void tile_stats(const cell_handle* h, cell_stats& S);
 template <> Krylov<double>& kry<double>(cell_handle* h) { return h->kd; }
 
 template <typename T> const T* rho_of(cell_handle* h);
@@ -340,7 +345,8 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
     if constexpr (sizeof(T) == 4) {
       const int kind = NC == 3 ? cell::NK_UU : cell::NK_SS4;
       if (h->nc_ok && h->d.opt.tensor_cores >= 1 &&
-          cell::apply_nc(kind, a, h->ncb + cell::nc_table_floats() * kind, mode, 9, h->tc_err, h->st)) {
+          cell::apply_nc(kind, a, h->ncb + cell::nc_table_floats() * kind, mode, 9, h->tc_err, h->st,
+                         h->nct[kind])) {
       } else if constexpr (NC == 3) {
         cell::apply_uu<T>(a, K.K0, mode, 9, h->st);
       } else {
@@ -1052,6 +1058,8 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
     CKS(setup_krylov<double>(h));
   }
   CKS(load_design(h, d->input));
+  if (h->nc_ok && d->opt.precision == CELL_MIXED_FP32 && d->opt.tensor_cores >= 1 && d->opt.autotune)
+    CKS(tune_tiles(h));
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   return CELL_OK;
@@ -1270,6 +1278,7 @@ int solve_graph_finish(cell_handle* h, cell_stats* st) {
   S.status = status;
   S.nlevels_u = (int)kry<T>(h).mgu.lv.size();
   S.nlevels_phi = (int)kry<T>(h).mgp.lv.size();
+  tile_stats(h, S);
   S.solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - h->gt0).count();
   h->solved = (status == CELL_OK);
   h->last = S;
@@ -1364,6 +1373,7 @@ int solve_impl(cell_handle* h, cell_stats* st) {
   S.status = status;
   S.nlevels_u = (int)kry<T>(h).mgu.lv.size();
   S.nlevels_phi = (int)kry<T>(h).mgp.lv.size();
+  tile_stats(h, S);
   if (h->prof.on) h->prof.collect(S.class_ms, S.class_count, S.class_units);
   h->solved = (status == CELL_OK);
   h->last = S;
@@ -1444,6 +1454,44 @@ void run_sensitivity(cell_handle* h, const cell::SensParams& P, T* g) {
 }  // namespace
 
 
+namespace {
+
+// Tile autotuning of the tensor-core smoothers (options.autotune): each
+// block's Chebyshev step on the fine level is timed for every tile candidate
+// on the handle's own scratch vectors (level-0 r, d, d2 and the Krylov basis,
+// all rewritten by every solve before use) and the fastest tile is kept.  The
+// tile changes launch geometry only, never a result.
+int tune_tiles(cell_handle* h) {
+  Krylov<float>& K = h->kf;
+  for (int kind = 0; kind < 2; ++kind) {
+    Level<float>& L0 = kind == cell::NK_UU ? K.mgu.lv[0] : K.mgp.lv[0];
+    const i64 ws = (kind == cell::NK_UU ? 3 : 1) * h->nn;
+    cell::ApplyArgs<float> a{};
+    a.x = L0.d; a.xs = ws; a.y = L0.r; a.ys = ws; a.sol = K.V; a.ss = ws; a.dout = L0.d2; a.ds = ws;
+    a.cc = L0.cc; a.sol_zero = 0;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    a.dinv = L0.dinv; a.rho = K.rho; a.cslot1 = h->cslot1;
+    h->nct[kind] = cell::nc_autotune(kind, a, h->ncb + cell::nc_table_floats() * kind, cell::AM_CHEB, 9,
+                                     h->tc_err, h->st, &h->nct_us[kind]);
+  }
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(cudaStreamSynchronize(h->st));
+  if (err) return CELL_ECUDA;   // a bounded wait expired: the tensor-core path is not usable
+  return CELL_OK;
+}
+
+void tile_stats(const cell_handle* h, cell_stats& S) {
+  const bool tc = h->nc_ok && h->d.opt.precision == CELL_MIXED_FP32 && h->d.opt.tensor_cores >= 1;
+  for (int k = 0; k < 2; ++k) {
+    S.tc_tile_xt[k] = tc ? h->nct[k].xt : 0;
+    S.tc_tile_L[k] = tc ? h->nct[k].L : 0;
+    S.tc_tile_us[k] = tc ? h->nct_us[k] : 0.0;
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 void cell_default_options(cell_options* o) {
@@ -1469,6 +1517,7 @@ void cell_default_options(cell_options* o) {
   o->graphs = 2;
   o->profile_mask = 0;
   o->precond = CELL_PRECOND_SCP;
+  o->autotune = 1;
 }
 
 int cell_setup(const cell_desc* d, cell_handle** out) {
@@ -1843,6 +1892,18 @@ int cell_apply(cell_handle* h, const void* x, void* y, int nrhs, int dtype) {
   return CELL_OK;
 }
 
+int cell_set_tile(cell_handle* h, int block, int xt, int L) {
+  if (!h || (block != CELL_BLOCK_A && block != CELL_BLOCK_SBAR)) return CELL_EINVAL;
+  if (!h->nc_ok || h->d.opt.precision != CELL_MIXED_FP32 || h->d.opt.tensor_cores < 1) return CELL_EINVAL;
+  const int xmax = h->nx >= 32 ? 32 : ((h->nx + 7) / 8) * 8;
+  const bool dflt = xt == 0 && L == 0;
+  if (!dflt && (!(xt == 8 || xt == 16 || xt == 32) || xt > xmax || L < 1)) return CELL_EINVAL;
+  const int kind = block == CELL_BLOCK_A ? cell::NK_UU : cell::NK_SS4;
+  h->nct[kind] = cell::NcTile{xt, L};
+  h->nct_us[kind] = 0.f;
+  return CELL_OK;
+}
+
 int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs, int dtype) {
   if (!h || !x || !y || nrhs < 1 || nrhs > 65535) return CELL_EINVAL;
   if (block != CELL_BLOCK_A && block != CELL_BLOCK_SBAR) return CELL_EINVAL;
@@ -1857,7 +1918,7 @@ int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs
       if (!h->nc_ok) return CELL_EINVAL;
       const int kind = nc == 3 ? cell::NK_UU : cell::NK_SS4;
       if (!cell::apply_nc(kind, a, h->ncb + cell::nc_table_floats() * kind, cell::AM_LINEAR, nrhs,
-                          h->tc_err, h->st))
+                          h->tc_err, h->st, h->nct[kind]))
         return CELL_EINVAL;
     } else if (nc == 3) {
       cell::FixedMat<float, 4> M;

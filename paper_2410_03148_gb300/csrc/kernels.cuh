@@ -167,9 +167,19 @@ bool nc_shape_ok(int nx, int ny, int nz);
 void nc_prepare();
 size_t nc_table_floats();
 void nc_build_b(int kind, const double* K0, const double* S0, float* out);
+// CTA tile: xt nodes along x (8, 16 or 32) by 16 rows, L z-planes per chunk;
+// 0 = the default (widest tile, wave-count heuristic for L).
+struct NcTile {
+  int xt, L;
+};
 // Returns false (nothing launched) if the grid would exceed the launch limits.
 bool apply_nc(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
-              cudaStream_t s);
+              cudaStream_t s, NcTile tile);
+// Times the tile candidates in the given mode on the caller's buffers (which
+// it overwrites like that mode does) and returns the fastest; synchronises s.
+// *best_us (if non-null) = its time per launch in microseconds.
+NcTile nc_autotune(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
+                   cudaStream_t s, float* best_us);
 
 // ---- multigrid helpers (mg.cu) ----------------------------------------------
 // r = b, d = c2 Dinv b with c2 read from device memory (*c2p)

@@ -125,3 +125,33 @@ def test_block_apply_tc_sampled_full_size(block, n):
         got = np.array([y[r, :, k, j, i] for (i, j, k) in nodes])
         err = np.abs(got - want)
         assert np.all(err <= 2.0 ** -9 * bound + 2e-6 * bound.max()), (err / bound).max()
+
+
+@pytest.mark.parametrize("shape", [(20, 18, 40), (9, 33, 64), (5, 6, 7)])
+def test_every_tensor_core_tile_gives_the_same_bits(shape):
+    """The autotuner may pick any CTA tile (x width 8/16/32, z-chunk length):
+    each one must give bitwise the result of the default tile, on ragged grids
+    (partial x tiles, partial 16-row y tiles, chunks that do not divide nz) and
+    for chunk lengths beyond nz.  Invalid tiles are rejected."""
+    from paper_2410_03148_gb300._binding import CellError
+    cell = make_cell(cellgen.random_rho(shape, seed=16))
+    nz, ny, nx = shape
+    xmax = 32 if nx >= 32 else (nx + 7) // 8 * 8
+    g = torch.Generator(dev()).manual_seed(3)
+    for block, nc in (("A", 3), ("Sbar", 1)):
+        x = torch.randn((9, nc) + shape, device=dev(), generator=g)
+        cell.set_tile(block, 0, 0)
+        ref = cell.apply_block(block, x, tensor_cores=True)
+        for xt in (8, 16, 32):
+            if xt > xmax:
+                continue
+            for L in sorted({1, 2, 3, 4, 7, 16, nz, nz + 5}):
+                cell.set_tile(block, xt, L)
+                y = cell.apply_block(block, x, tensor_cores=True)
+                assert torch.equal(y, ref), (block, xt, L)
+    for bad in ((24, 4), (8, 0), (-8, 4), (64, 4)):
+        with pytest.raises(CellError):
+            cell.set_tile("A", *bad)
+    if xmax < 32:
+        with pytest.raises(CellError):
+            cell.set_tile("Sbar", 32, 4)

@@ -588,3 +588,19 @@ def test_all_void_level_set(precision):
     assert np.abs(Ch - 1e-3 * C).max() < 1e-12 * 1e-3 * np.abs(C).max()
     assert np.abs(eh - 1e-3 * e).max() < 1e-12 * 1e-3 * np.abs(e).max()
     assert np.abs(kh - 1e-3 * k).max() < 1e-12 * 1e-3 * np.abs(k).max()
+
+
+def test_autotuned_tiles_leave_the_solve_unchanged():
+    """cell_setup's tile autotuner (on by default) changes launch geometry
+    only: the solve with tuned tiles equals the one with the default tiles
+    bitwise, and the stats report the tuned tiles."""
+    phi = cellgen.gaussian_levelset(24, seed=31)
+    a = make_cell(phi, "phi", autotune=0)
+    b = make_cell(phi, "phi", autotune=1)
+    sa, sb = a.solve(), b.solve()
+    assert sa["iters"] == sb["iters"] and sa["refinements"] == sb["refinements"]
+    for x, y in zip(a.homogenise(), b.homogenise()):
+        assert np.array_equal(x, y)
+    assert all(t["xt"] == 0 and t["L"] == 0 for t in sa["tc_tiles"])
+    for t in sb["tc_tiles"]:
+        assert t["xt"] in (8, 16, 32) and 1 <= t["L"] <= 24 and t["us"] > 0
