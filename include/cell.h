@@ -116,8 +116,11 @@ typedef struct cell_options {
                           caller's stream; 2 (default) = the whole solve captured once per
                           handle into one graph whose refinement loop (a WHILE node) and
                           Arnoldi steps (IF nodes) are controlled by device kernels, so a
-                          solve is one launch and one synchronisation.  With profile set,
-                          2 behaves as 1 (event timings need the host loop).  The first
+                          solve is one launch and one synchronisation; cell_solve_batch
+                          then puts all handles' solves into one graph (one launch per
+                          batch); 3 = as 2, but cell_solve_batch launches each handle's
+                          graph separately on its own stream.  With profile set, 2 and 3
+                          behave as 1 (event timings need the host loop).  The first
                           solve of a handle pays the capture. */
   int profile_mask;    /* with profile set: bit c (cell_prof_class) = time class c;
                           0 = every class */
@@ -126,7 +129,9 @@ typedef struct cell_options {
                           the tensor-core smoothers' CTA tiles (x width 8/16/32 nodes, z-chunk
                           length) on this GPU and grid and keep the fastest per block (cell_stats
                           reports them); every tile gives bitwise the same result.  0 = widest
-                          tile and a wave-count heuristic. */
+                          tile and a wave-count heuristic.  MIXED (any tensor_cores): nonzero also
+                          times the coarse levels' stencil apply with 1, 3 and 9 loads per thread
+                          and keeps the fastest per level (bitwise-neutral; cell_stats.stencil_rg). */
 } cell_options;
 
 typedef enum cell_precond {
@@ -179,6 +184,10 @@ typedef struct cell_stats {
                                        A, [1] Schur Sbar): x width in nodes and z-chunk length;
                                        0 = not tuned (default tile or SIMT path) */
   double tc_tile_us[2];             /* the tuned tile's time per 9-load Chebyshev launch, us */
+  int stencil_rg[2][8];             /* MIXED: loads per thread of the coarse stencil apply per
+                                       multigrid level ([0] elastic, [1] Schur; level 0 = fine
+                                       grid, always 0); 0 = size default, 1/3/9 = tuned at set-up
+                                       (options.autotune; bitwise-neutral) */
 } cell_stats;
 
 typedef struct cell_handle cell_handle;
@@ -213,14 +222,22 @@ int cell_update(cell_handle* h, const void* input);
  * usable best solution) if tol was not reached within max_iter/max_refine. */
 int cell_solve(cell_handle* h, cell_stats* st);
 
-/* cell_solve for n distinct handles (cells of any sizes and options).  If
- * every handle runs whole-solve graphs (graphs = 2, no profiling), the calling
- * thread launches all the solves and then collects them; otherwise up to 16
- * host threads drive one handle each.  Handles on different streams solve
- * concurrently on the GPU, handles sharing a stream one after another.  st: NULL or n
- * stats (st[i].status holds handle i's result).  Returns CELL_OK, or the
- * status of the first handle (in list order) that failed; CELL_EINVAL for
- * a NULL list entry or a handle listed twice (nothing solved). */
+/* cell_solve for n distinct handles (cells of any sizes and options).
+ * If every handle runs whole-solve graphs with graphs = 2 (no profiling) on
+ * one device, the n solves are built into ONE executable CUDA graph, each an
+ * independent branch with its own device-controlled refinement loop and
+ * Arnoldi steps, and the batch is a single graph launch on hs[0]'s stream
+ * (ordered after the work queued on every handle's stream; every handle's
+ * stream is ordered after the batch).  The graph of the last batch is kept
+ * and relaunched while the same handles are passed in the same order; the
+ * first call of a new list pays the capture.  With graphs = 3 on every handle
+ * (or handles on several devices), the calling thread launches one graph per
+ * handle on the handle's stream; otherwise up to 16 host threads drive one
+ * handle each.  Results are bitwise those of cell_solve on each handle.
+ * st: NULL or n stats (st[i].status holds handle i's result).  Returns
+ * CELL_OK, or the status of the first handle (in list order) that failed;
+ * CELL_EINVAL for a NULL list entry or a handle listed twice (nothing solved).
+ * Not thread-safe for handles shared between concurrent calls. */
 int cell_solve_batch(cell_handle** hs, int n, cell_stats* st);
 
 /* Homogenised tensors of the last solve (Eqs. hom_C, hom_e, hom_kappa with
@@ -362,6 +379,17 @@ int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs
  * or a handle without the tensor-core path (FP64 precision, tensor_cores = 0
  * or a grid it does not support). */
 int cell_set_tile(cell_handle* h, int block, int xt, int L);
+
+/* Set the loads per thread (rg = 1, 3 or 9; 0 = the size default) of the
+ * assembled-stencil apply on multigrid level `level` (>= 1) of one block
+ * (cell_block), replacing the value cell_setup tuned.  Results do not depend
+ * on rg (every (node, load) runs the same operation sequence); it changes
+ * launch geometry and speed only.  Takes effect for later launches; a solve
+ * graph captured before the call keeps the value it was captured with.
+ * Levels small enough for the four-lane stencil kernel ignore it.  Errors:
+ * CELL_EINVAL for a null handle, an unknown block, a level outside
+ * 1 .. levels-1, an rg not in {0, 1, 3, 9}, or FP64 precision. */
+int cell_set_stencil_rg(cell_handle* h, int block, int level, int rg);
 
 /* The nine right-hand sides bhat = S_phi (-sum_e rho_e P_e^T K0 Zbar_e^I) as
  * FP64 cell vectors into the DEVICE buffer out (9*4*N values). */

@@ -28,7 +28,7 @@ EXPORTS = [
     "cell_default_options", "cell_setup", "cell_update", "cell_solve", "cell_solve_batch", "cell_homogenise",
     "cell_sensitivity", "cell_sensitivity_phi", "cell_hj_step",
     "cell_dh", "cell_figure", "cell_get_solution", "cell_apply", "cell_apply_block", "cell_rhs", "cell_get_rho",
-    "cell_element_matrices", "cell_homogenise_noalloc", "cell_energy_difference", "cell_hilbert_velocity", "cell_set_tile", "cell_launch_count", "cell_destroy",
+    "cell_element_matrices", "cell_homogenise_noalloc", "cell_energy_difference", "cell_hilbert_velocity", "cell_set_tile", "cell_set_stencil_rg", "cell_launch_count", "cell_destroy",
     "cell_status_str", "cell_last_error",
 ]
 
@@ -66,6 +66,7 @@ class cell_stats(C.Structure):
         ("class_count", C.c_int * len(PROF_CLASSES)),
         ("class_units", C.c_longlong * len(PROF_CLASSES)),
         ("tc_tile_xt", C.c_int * 2), ("tc_tile_L", C.c_int * 2), ("tc_tile_us", C.c_double * 2),
+        ("stencil_rg", (C.c_int * 8) * 2),
     ]
 
 
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
     lib.cell_apply.argtypes = [P, P, P, C.c_int, C.c_int]
     lib.cell_apply_block.argtypes = [P, C.c_int, P, P, C.c_int, C.c_int]
     lib.cell_set_tile.argtypes = [P, C.c_int, C.c_int, C.c_int]
+    lib.cell_set_stencil_rg.argtypes = [P, C.c_int, C.c_int, C.c_int]
     lib.cell_rhs.argtypes = [P, P]
     lib.cell_get_rho.argtypes = [P, P]
     lib.cell_element_matrices.argtypes = [C.POINTER(cell_desc), D, D]
@@ -302,6 +304,10 @@ def cell_apply_block(h, block: int, x_ptr: int, y_ptr: int, nrhs: int, dtype: in
 
 def cell_set_tile(h, block: int, xt: int, L: int):
     _check("cell_set_tile", load().cell_set_tile(h, block, xt, L))
+
+
+def cell_set_stencil_rg(h, block: int, level: int, rg: int):
+    _check("cell_set_stencil_rg", load().cell_set_stencil_rg(h, block, level, rg))
 
 
 def cell_rhs(h, out_ptr: int):

@@ -30,6 +30,7 @@ def _stats_dict(status, st):
         "nlevels_u": st.nlevels_u,
         "nlevels_phi": st.nlevels_phi,
         "tc_tiles": [{"xt": st.tc_tile_xt[k], "L": st.tc_tile_L[k], "us": st.tc_tile_us[k]} for k in range(2)],
+        "stencil_rg": [list(st.stencil_rg[k]) for k in range(2)],
     }
 
 
@@ -151,6 +152,12 @@ class Cell:
         along x: 8, 16 or 32; L z-planes per chunk); 0, 0 = the default tile."""
         blk = B.CELL_BLOCK_A if block == "A" else B.CELL_BLOCK_SBAR
         B.cell_set_tile(self._h, blk, xt, L)
+
+    def set_stencil_rg(self, block: str, level: int, rg: int = 0) -> None:
+        """Fix the loads per thread (1, 3 or 9; 0 = default) of the coarse
+        stencil apply on multigrid level `level` of block "A" or "Sbar"."""
+        blk = B.CELL_BLOCK_A if block == "A" else B.CELL_BLOCK_SBAR
+        B.cell_set_stencil_rg(self._h, blk, level, rg)
 
     def rhs(self) -> torch.Tensor:
         out = torch.empty((9, 4) + self.shape, dtype=torch.float64, device=self.device)

@@ -33,12 +33,10 @@ struct NodeIdx {
 
 // Grid (ceil(nx*ny / kBlock), nz, nrhs): thread -> node (i, j, k) with 32-bit
 // index arithmetic; returns false past the end of the xy plane.
-__device__ __forceinline__ bool node_index(int nx, int ny, int nz, NodeIdx& t) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ bool node_index_at(int p, int k, int nx, int ny, int nz, NodeIdx& t) {
   if (p >= nx * ny) return false;
   const int j = p / nx;
   const int i = p - j * nx;
-  const int k = blockIdx.y;
   const i64 nxy = (i64)nx * ny;
   t.nn = nxy * nz;
   t.n = (i64)k * nxy + p;
@@ -54,12 +52,16 @@ __device__ __forceinline__ bool node_index(int nx, int ny, int nz, NodeIdx& t) {
   return true;
 }
 
+// Grid (plane blocks, planes, load groups).
+__device__ __forceinline__ bool node_index(int nx, int ny, int nz, NodeIdx& t) {
+  return node_index_at(blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y, nx, ny, nz, t);
+}
+
 // Store the NCO output components of one node according to MODE.
 // acc = (A x)_node, dold = this node's own gathered input (CHEB modes).
 template <typename T, int NCO, int MODE>
 __device__ __forceinline__ void epilogue(const ApplyArgs<T>& a, int r, const NodeIdx& t,
                                          const T* acc, const T* dold) {
-#pragma unroll
   T c1 = a.c1, c2 = a.c2;
   if (MODE != AM_LINEAR && a.cc) {
     c1 = a.cc[0];
@@ -401,12 +403,16 @@ __global__ void __launch_bounds__(kBlock) k_apply_elem(const ApplyArgs<T> a, int
 // Assembled block stencil on a coarse level: y_n = sum_q S_n[q] x_{n+q} over the
 // 27 neighbours q (offsets in {-1,0,1}^3, q = dx + 3 dy + 9 dz).  One thread per
 // node and group of RG loads; the node's stencil row (27 NC x NC blocks) is
-// read once per group with coalesced loads.
+// read once per group with coalesced loads.  Grid (load groups, plane blocks,
+// planes): the groups of one block of nodes are adjacent in launch order and
+// run at the same time, so the stencil rows that the first group brings from
+// DRAM are L2 hits for the others (a level-1 stencil of a 128^3 cell, 255 MB,
+// does not stay in L2 between groups launched a whole grid apart).
 template <typename T, int NC, int RG, int MODE>
 __global__ void __launch_bounds__(kBlock) k_apply_st(const ApplyArgs<T> a, int nrhs) {
   NodeIdx t;
-  if (!node_index(a.nx, a.ny, a.nz, t)) return;
-  const int r0 = blockIdx.z * RG;
+  if (!node_index_at(blockIdx.y * blockDim.x + threadIdx.x, blockIdx.z, a.nx, a.ny, a.nz, t)) return;
+  const int r0 = blockIdx.x * RG;
   bool on[RG];
   bool any = false;
 #pragma unroll
@@ -761,7 +767,8 @@ void apply_elem(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
 
 template <typename T, int NC, int RG>
 void launch_st(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
-  const dim3 g = grid_for(a, (nrhs + RG - 1) / RG);
+  const dim3 g0 = grid_for(a, (nrhs + RG - 1) / RG);
+  const dim3 g(g0.z, g0.x, g0.y);   // load groups fastest (see k_apply_st)
   switch (mode) {
     case AM_LINEAR: note_launch(), k_apply_st<T, NC, RG, AM_LINEAR><<<g, kBlock, 0, s>>>(a, nrhs); break;
     case AM_CHEB: note_launch(), k_apply_st<T, NC, RG, AM_CHEB><<<g, kBlock, 0, s>>>(a, nrhs); break;
@@ -782,15 +789,54 @@ void launch_st_split(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) 
 }
 
 template <typename T, int NC>
-void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s) {
+void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s, int rg) {
   const long long nn = (long long)a.nx * a.ny * a.nz;
-  // three loads per thread on large levels: all nine per thread reads the
-  // stencil once per apply but chains 27 rounds of 36 loads per thread, and
-  // the coarse levels of a 128^3 step measured slower with it (68.8 against
-  // 61.8 ms per step)
-  if (nn > 16384) launch_st<T, NC, 3>(a, mode, nrhs, s);
-  else if (nn > kSplitMaxNodes) launch_st<T, NC, 1>(a, mode, nrhs, s);
-  else launch_st_split<T, NC>(a, mode, nrhs, s);
+  if (nn <= kSplitMaxNodes) {
+    launch_st_split<T, NC>(a, mode, nrhs, s);
+    return;
+  }
+  // loads per thread: the tuned value, else three on large levels (all nine
+  // per thread chains 27 rounds of 36 loads per thread) and one below
+  if (rg <= 0) rg = nn > 16384 ? 3 : 1;
+  if (rg == 9) launch_st<T, NC, 9>(a, mode, nrhs, s);
+  else if (rg == 3) launch_st<T, NC, 3>(a, mode, nrhs, s);
+  else launch_st<T, NC, 1>(a, mode, nrhs, s);
+}
+
+// Loads per thread of the coarse stencil apply, timed on the caller's level
+// buffers (a as for apply_stencil, in the given mode).  Every choice computes
+// each (node, load) with the same operation sequence, so the results are
+// bitwise the same; candidates 1, 3 and 9, one warm-up and three timed
+// launches each between CUDA events on the stream.  Returns 0 (keep the
+// default) on levels that use the four-lane kernel or if nothing was timed.
+template <typename T, int NC>
+int stencil_autotune(const ApplyArgs<T>& a, int mode, int nrhs, cudaStream_t s, float* best_us) {
+  constexpr int kReps = 3;
+  if (best_us) *best_us = 0.f;
+  if ((long long)a.nx * a.ny * a.nz <= kSplitMaxNodes) return 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return 0;
+  }
+  int best = 0;
+  float best_t = 3.0e38f;
+  for (int rg : {1, 3, 9}) {
+    apply_stencil<T, NC>(a, mode, nrhs, s, rg);
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < kReps; ++r) apply_stencil<T, NC>(a, mode, nrhs, s, rg);
+    cudaEventRecord(e1, s);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+    if (ms < best_t) {
+      best_t = ms;
+      best = rg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best && best_us) *best_us = best_t * 1000.f / kReps;
+  return best;
 }
 
 template <typename T, int NC>
@@ -897,8 +943,10 @@ void cslot_release(int slot1) {
   template void apply_ss<T>(const ApplyArgs<T>&, const FixedMat<T, 1>&, int, int, cudaStream_t);   \
   template void apply_elem<T, 1>(const ApplyArgs<T>&, int, int, cudaStream_t);                     \
   template void apply_elem<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t);                     \
-  template void apply_stencil<T, 1>(const ApplyArgs<T>&, int, int, cudaStream_t);                  \
-  template void apply_stencil<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t);                  \
+  template void apply_stencil<T, 1>(const ApplyArgs<T>&, int, int, cudaStream_t, int);             \
+  template void apply_stencil<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t, int);             \
+  template int stencil_autotune<T, 1>(const ApplyArgs<T>&, int, int, cudaStream_t, float*);        \
+  template int stencil_autotune<T, 3>(const ApplyArgs<T>&, int, int, cudaStream_t, float*);        \
   template void stencil_from_elem<T, 1>(const T*, T*, int, int, int, cudaStream_t);                \
   template void stencil_from_elem<T, 3>(const T*, T*, int, int, int, cudaStream_t);
 INST(float)

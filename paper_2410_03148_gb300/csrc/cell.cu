@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -192,6 +193,7 @@ struct Level {
   T *b = nullptr, *x = nullptr, *r = nullptr, *d = nullptr, *d2 = nullptr;  // [9][NC][nn]
   T* cc = nullptr;       // Chebyshev coefficients on the device: (0, 1/theta), (c1_k, c2_k)
   int deg = 0;           // Chebyshev steps of this level
+  int rg = 0;            // loads per thread of the stencil apply (0 = default; tuned at set-up)
   T* dense = nullptr;    // coarsest: regularised inverse (n x n, symmetric)
   int ndense = 0;
   bool coarsest = false;
@@ -278,7 +280,7 @@ struct cell_handle {
   // an internal stream at first use and replayed on the caller's stream
   std::vector<IterGraph> graphs;
   cudaStream_t cap_st = nullptr;
-  // whole-solve graph (options.graphs == 2): device-side control state and
+  // whole-solve graph (options.graphs >= 2): device-side control state and
   // the kernels per captured segment (for cell_launch_count)
   cudaGraphExec_t solve_exec = nullptr;
   int solve_prec = -1;
@@ -315,6 +317,7 @@ template <typename T> Krylov<T>& kry(cell_handle* h);
 template <> Krylov<float>& kry<float>(cell_handle* h) { return h->kf; }
 
 int tune_tiles(cell_handle* h);
+template <typename T, int NC> void tune_stencils(cell_handle* h, BlockMG<T>& mg);
 void tile_stats(const cell_handle* h, cell_stats& S);
 template <> Krylov<double>& kry<double>(cell_handle* h) { return h->kd; }
 
@@ -359,7 +362,7 @@ void level_apply(cell_handle* h, BlockMG<T>& mg, int l, int mode, const cell::Ap
     }
   } else {
     a.st = L.st;
-    cell::apply_stencil<T, NC>(a, mode, 9, h->st);
+    cell::apply_stencil<T, NC>(a, mode, 9, h->st, L.rg);
   }
   h->prof.end(pcls, ip, h->st);
 }
@@ -866,7 +869,7 @@ int check_options(const cell_options& o) {
   if ((o.load_mask & 0x1FF) == 0 || (o.load_mask & ~0x1FF)) return CELL_EINVAL;
   if (o.tensor_cores < 0 || o.tensor_cores > 2) return CELL_EINVAL;
   if (o.precond != CELL_PRECOND_SCP && o.precond != CELL_PRECOND_DBP) return CELL_EINVAL;
-  if (o.graphs < 0 || o.graphs > 2) return CELL_EINVAL;
+  if (o.graphs < 0 || o.graphs > 3) return CELL_EINVAL;
   return CELL_OK;
 }
 
@@ -1060,13 +1063,17 @@ int setup_impl(const cell_desc* d, cell_handle* h) {
   CKS(load_design(h, d->input));
   if (h->nc_ok && d->opt.precision == CELL_MIXED_FP32 && d->opt.tensor_cores >= 1 && d->opt.autotune)
     CKS(tune_tiles(h));
+  if (d->opt.precision == CELL_MIXED_FP32 && d->opt.autotune) {
+    tune_stencils<float, 3>(h, h->kf.mgu);
+    tune_stencils<float, 1>(h, h->kf.mgp);
+  }
   CK(cudaStreamSynchronize(h->st));
   CK(cudaGetLastError());
   return CELL_OK;
 }
 
 // ---------------------------------------------------------------------------
-// whole solve as one graph (options.graphs == 2)
+// whole solve as one graph (options.graphs >= 2)
 // ---------------------------------------------------------------------------
 
 template <typename T>
@@ -1134,16 +1141,17 @@ cudaError_t add_conditional(cell_handle* h, cudaGraphConditionalHandle c, cudaGr
 //           cycle end (least squares, x += Z y, residual, |r|^2, control)
 //         }
 //         epilogue (null-space projection)
+//
+// The solve is added to `top` as an independent branch (its first nodes have
+// no dependencies), so several handles' solves can share one graph.
 template <typename T>
-int build_solve_graph(cell_handle* h) {
+int add_solve_graph(cell_handle* h, cudaGraph_t top) {
   Krylov<T>& K = kry<T>(h);
   const int m = K.m;
   const i64 len = K.len;
   const int nblk = h->nblk;
   const cell::CtlParams P = ctl_params<T>(h);
   if (!h->cap_st) CK(cudaStreamCreateWithFlags(&h->cap_st, cudaStreamNonBlocking));
-  cudaGraph_t top = nullptr;
-  CK(cudaGraphCreate(&top, 0));
   cudaGraphConditionalHandle wh;
   cudaError_t e = cudaGraphConditionalHandleCreate(&wh, top, 0, cudaGraphCondAssignDefault);
   cudaGraph_t wbody = nullptr;
@@ -1224,10 +1232,7 @@ int build_solve_graph(cell_handle* h) {
     }, &n_it);
     if (j == 0) n_it0 = n_it;
   }
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->solve_exec, top, 0);
-  cudaGraphDestroy(top);
   if (e != cudaSuccess) {
-    h->solve_exec = nullptr;
     set_error("whole-solve CUDA graph (conditional nodes)", e);
     return CELL_ECUDA;
   }
@@ -1235,7 +1240,35 @@ int build_solve_graph(cell_handle* h) {
   h->seg_pro = n_top - n_epi;
   h->seg_cb = n_body - h->seg_ce;
   h->seg_it = n_it0;   // kernels per Arnoldi step (the last step of a cycle has one fewer)
-  h->solve_prec = sizeof(T) == 4 ? 1 : 0;
+  return CELL_OK;
+}
+
+template <typename T>
+int build_solve_graph(cell_handle* h) {
+  cudaGraph_t top = nullptr;
+  CK(cudaGraphCreate(&top, 0));
+  int rc = add_solve_graph<T>(h, top);
+  if (rc == CELL_OK) {
+    const cudaError_t e = cudaGraphInstantiate(&h->solve_exec, top, 0);
+    if (e != cudaSuccess) {
+      h->solve_exec = nullptr;
+      set_error("whole-solve CUDA graph (conditional nodes)", e);
+      rc = CELL_ECUDA;
+    }
+  }
+  cudaGraphDestroy(top);
+  if (rc == CELL_OK) h->solve_prec = sizeof(T) == 4 ? 1 : 0;
+  return rc;
+}
+
+// Asynchronous copy of a graph solve's statistics to the pinned host block,
+// ordered after the solve on stream s.
+int copy_solve_stats(cell_handle* h, cudaStream_t s) {
+  cell_handle::GraphStats* G = h->gstat;
+  CK(cudaMemcpyAsync(G->ctl, h->ctl_d, sizeof(G->ctl), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(G->iters, h->iters_d, sizeof(G->iters), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(G->relres, h->relres_d, sizeof(G->relres), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(&G->tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   return CELL_OK;
 }
 
@@ -1245,14 +1278,8 @@ template <typename T>
 int solve_graph_launch(cell_handle* h) {
   h->gt0 = std::chrono::steady_clock::now();
   if (!h->solve_exec || h->solve_prec != (sizeof(T) == 4 ? 1 : 0)) CKS(build_solve_graph<T>(h));
-  cudaStream_t s = h->st;
-  cell_handle::GraphStats* G = h->gstat;
-  CK(cudaGraphLaunch(h->solve_exec, s));
-  CK(cudaMemcpyAsync(G->ctl, h->ctl_d, sizeof(G->ctl), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(G->iters, h->iters_d, sizeof(G->iters), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(G->relres, h->relres_d, sizeof(G->relres), cudaMemcpyDeviceToHost, s));
-  CK(cudaMemcpyAsync(&G->tcerr, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
-  return CELL_OK;
+  CK(cudaGraphLaunch(h->solve_exec, h->st));
+  return copy_solve_stats(h, h->st);
 }
 
 template <typename T>
@@ -1295,7 +1322,7 @@ int solve_graph(cell_handle* h, cell_stats* st) {
 template <typename T>
 int solve_impl(cell_handle* h, cell_stats* st) {
   const cell_options& o = h->d.opt;
-  if (o.graphs == 2 && !h->prof.on) return solve_graph<T>(h, st);
+  if (o.graphs >= 2 && !h->prof.on) return solve_graph<T>(h, st);
   cudaStream_t s = h->st;
   const i64 len = 4 * h->nn;
   const int nblk = h->nblk;
@@ -1481,6 +1508,22 @@ int tune_tiles(cell_handle* h) {
   return CELL_OK;
 }
 
+// Loads per thread of every coarse level's stencil apply, timed at set-up in
+// the Chebyshev mode on the level's own scratch vectors (bitwise-neutral).
+template <typename T, int NC>
+void tune_stencils(cell_handle* h, BlockMG<T>& mg) {
+  for (size_t l = 1; l < mg.lv.size(); ++l) {
+    Level<T>& L = mg.lv[l];
+    if (!L.st || L.dense) continue;
+    const i64 ws = NC * L.nn;
+    cell::ApplyArgs<T> a{};
+    a.x = L.d; a.xs = ws; a.y = L.r; a.ys = ws; a.sol = L.x; a.ss = ws; a.dout = L.d2; a.ds = ws;
+    a.dinv = L.dinv; a.cc = L.cc; a.st = L.st;
+    a.nx = L.nx; a.ny = L.ny; a.nz = L.nz;
+    L.rg = cell::stencil_autotune<T, NC>(a, cell::AM_CHEB, 9, h->st, nullptr);
+  }
+}
+
 void tile_stats(const cell_handle* h, cell_stats& S) {
   const bool tc = h->nc_ok && h->d.opt.precision == CELL_MIXED_FP32 && h->d.opt.tensor_cores >= 1;
   for (int k = 0; k < 2; ++k) {
@@ -1488,6 +1531,105 @@ void tile_stats(const cell_handle* h, cell_stats& S) {
     S.tc_tile_L[k] = tc ? h->nct[k].L : 0;
     S.tc_tile_us[k] = tc ? h->nct_us[k] : 0.0;
   }
+  if (h->d.opt.precision == CELL_MIXED_FP32) {
+    const auto& u = h->kf.mgu.lv;
+    const auto& p = h->kf.mgp.lv;
+    for (int l = 0; l < 8; ++l) {
+      S.stencil_rg[0][l] = l < (int)u.size() ? u[l].rg : 0;
+      S.stencil_rg[1][l] = l < (int)p.size() ? p[l].rg : 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one graph for a batch of solves
+// ---------------------------------------------------------------------------
+
+// The whole-solve graphs of several handles (same device) as independent
+// branches of one executable graph: a batch is one graph launch, and the
+// solves run concurrently however their iteration counts differ (each
+// branch's refinement loop and Arnoldi steps are its own conditional nodes).
+// The executable graph of the last batch is kept and reused while the same
+// handles, in the same order, are solved again; destroying one of them drops it.
+struct BatchGraph {
+  std::vector<cell_handle*> hs;
+  std::vector<int> prec;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t ev = nullptr;
+  int dev = -1;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ev) cudaEventDestroy(ev);
+    exec = nullptr;
+    ev = nullptr;
+    hs.clear();
+    prec.clear();
+    dev = -1;
+  }
+};
+std::mutex g_batch_mu;
+BatchGraph g_batch;
+
+int prec_of(const cell_handle* h) { return h->d.opt.precision == CELL_MIXED_FP32 ? 1 : 0; }
+
+// Build (or reuse) the batch graph of hs[0..n) and launch it on hs[0]'s
+// stream, ordered after the work already queued on every handle's stream;
+// every handle's stream is ordered after the batch and its statistics copy.
+int solve_batch_graph(cell_handle** hs, int n) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  BatchGraph& B = g_batch;
+  bool same = B.exec && (int)B.hs.size() == n && B.dev == hs[0]->dev;
+  for (int i = 0; same && i < n; ++i) same = B.hs[i] == hs[i] && B.prec[i] == prec_of(hs[i]);
+  CK(cudaSetDevice(hs[0]->dev));
+  const auto t0 = std::chrono::steady_clock::now();
+  if (!same) {
+    B.reset();
+    cudaGraph_t top = nullptr;
+    CK(cudaGraphCreate(&top, 0));
+    int rc = CELL_OK;
+    for (int i = 0; i < n && rc == CELL_OK; ++i)
+      rc = prec_of(hs[i]) ? add_solve_graph<float>(hs[i], top) : add_solve_graph<double>(hs[i], top);
+    if (rc == CELL_OK) {
+      const cudaError_t e = cudaGraphInstantiate(&B.exec, top, 0);
+      if (e != cudaSuccess) {
+        B.exec = nullptr;
+        set_error("batched whole-solve CUDA graph", e);
+        rc = CELL_ECUDA;
+      }
+    }
+    cudaGraphDestroy(top);
+    if (rc == CELL_OK && cudaEventCreateWithFlags(&B.ev, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("cudaEventCreateWithFlags");
+      rc = CELL_ECUDA;
+    }
+    if (rc != CELL_OK) {
+      B.reset();
+      return rc;
+    }
+    B.hs.assign(hs, hs + n);
+    for (int i = 0; i < n; ++i) B.prec.push_back(prec_of(hs[i]));
+    B.dev = hs[0]->dev;
+  }
+  cudaStream_t L = hs[0]->st;
+  for (int i = 1; i < n; ++i) {
+    CK(cudaEventRecord(B.ev, hs[i]->st));
+    CK(cudaStreamWaitEvent(L, B.ev, 0));
+  }
+  for (int i = 0; i < n; ++i) hs[i]->gt0 = t0;
+  CK(cudaGraphLaunch(B.exec, L));
+  for (int i = 0; i < n; ++i) CKS(copy_solve_stats(hs[i], L));
+  CK(cudaEventRecord(B.ev, L));
+  for (int i = 1; i < n; ++i) CK(cudaStreamWaitEvent(hs[i]->st, B.ev, 0));
+  return CELL_OK;
+}
+
+void forget_batch(const cell_handle* h) {
+  std::lock_guard<std::mutex> lock(g_batch_mu);
+  for (const cell_handle* q : g_batch.hs)
+    if (q == h) {
+      g_batch.reset();
+      return;
+    }
 }
 
 }  // namespace
@@ -1580,15 +1722,24 @@ int cell_solve_batch(cell_handle** hs, int n, cell_stats* st) {
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return CELL_EINVAL;
   }
-  // whole-solve graphs: launch every handle's solve (one graph each, on its
-  // own stream), then collect the statistics; the host never waits between
-  // launches, so solves on different streams overlap on the GPU
-  bool all_graphs = true;
-  for (int i = 0; i < n; ++i) all_graphs = all_graphs && hs[i]->d.opt.graphs == 2 && !hs[i]->prof.on;
+  // whole-solve graphs: with graphs == 2 on every handle of one device, all
+  // solves are branches of one graph and the batch is one launch; with
+  // graphs == 3 (or handles on several devices), every handle's solve graph is
+  // launched on its own stream.  The host never waits between launches, so the
+  // solves overlap on the GPU; the statistics are collected afterwards.
+  bool all_graphs = true, one_graph = n > 1;
+  for (int i = 0; i < n; ++i) {
+    all_graphs = all_graphs && hs[i]->d.opt.graphs >= 2 && !hs[i]->prof.on;
+    one_graph = one_graph && hs[i]->d.opt.graphs == 2 && hs[i]->dev == hs[0]->dev;
+  }
   if (all_graphs) {
     std::vector<int> rc(n, CELL_OK);
     std::vector<std::string> errs(n);
-    for (int i = 0; i < n; ++i) {
+    if (one_graph) {
+      const int r = solve_batch_graph(hs, n);
+      if (r != CELL_OK) return r;
+    }
+    for (int i = 0; i < n && !one_graph; ++i) {
       cell_handle* h = hs[i];
       if (cudaSetDevice(h->dev) != cudaSuccess) {
         rc[i] = CELL_ECUDA;
@@ -1904,6 +2055,15 @@ int cell_set_tile(cell_handle* h, int block, int xt, int L) {
   return CELL_OK;
 }
 
+int cell_set_stencil_rg(cell_handle* h, int block, int level, int rg) {
+  if (!h || (block != CELL_BLOCK_A && block != CELL_BLOCK_SBAR)) return CELL_EINVAL;
+  if (h->d.opt.precision != CELL_MIXED_FP32 || !(rg == 0 || rg == 1 || rg == 3 || rg == 9)) return CELL_EINVAL;
+  auto& lv = block == CELL_BLOCK_A ? h->kf.mgu.lv : h->kf.mgp.lv;
+  if (level < 1 || level >= (int)lv.size()) return CELL_EINVAL;
+  lv[level].rg = rg;
+  return CELL_OK;
+}
+
 int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs, int dtype) {
   if (!h || !x || !y || nrhs < 1 || nrhs > 65535) return CELL_EINVAL;
   if (block != CELL_BLOCK_A && block != CELL_BLOCK_SBAR) return CELL_EINVAL;
@@ -1977,6 +2137,7 @@ int cell_element_matrices(const cell_desc* d, double K0[1024], double S0[64]) {
 void cell_destroy(cell_handle* h) {
   if (!h) return;
   cudaStreamSynchronize(h->st);
+  forget_batch(h);
   h->free_graphs();
   cell::cslot_release(h->cslot1);
   h->arena.release();

@@ -117,9 +117,13 @@ template <typename T> void apply_ss(const ApplyArgs<T>& a, const FixedMat<T, 1>&
 // Per-element-matrix operator on a coarse level (NC = 1 or 3).
 template <typename T, int NC> void apply_elem(const ApplyArgs<T>& a, int mode, int nrhs,
                                               cudaStream_t s);
-// Assembled-stencil operator on a coarse level (NC = 1 or 3), a.st set.
+// Assembled-stencil operator on a coarse level (NC = 1 or 3), a.st set; rg =
+// loads per thread (1, 3 or 9; 0 = size heuristic), bitwise-neutral.
 template <typename T, int NC> void apply_stencil(const ApplyArgs<T>& a, int mode, int nrhs,
-                                                 cudaStream_t s);
+                                                 cudaStream_t s, int rg = 0);
+// Fastest rg for apply_stencil on this level (timed on a's buffers); 0 = default.
+template <typename T, int NC> int stencil_autotune(const ApplyArgs<T>& a, int mode, int nrhs,
+                                                   cudaStream_t s, float* best_us);
 // Assemble the 27-point block stencil of a level from its element matrices.
 template <typename T, int NC> void stencil_from_elem(const T* ke, T* st, int nx, int ny, int nz,
                                                      cudaStream_t s);

@@ -371,28 +371,51 @@ def test_nonpositive_rho_is_rejected():
         make_cell(rho, "rho")
 
 
-def test_solve_batch_matches_individual_solves():
+@pytest.mark.parametrize("graphs", [2, 3])
+def test_solve_batch_matches_individual_solves(graphs):
     """cell_solve_batch on cells of different sizes and precisions, each on its
     own stream: every result equals (bitwise) the cell solved alone, and the
-    8^3 one matches the oracle."""
+    8^3 one matches the oracle.  graphs = 2 runs the batch as one graph launch:
+    the graph is reused after new designs are mapped into the same handles,
+    and rebuilt when a handle of the batch is destroyed; graphs = 3 launches
+    one graph per handle."""
     from paper_2410_03148_gb300 import solve_batch
     cases = [((8, 8, 8), 1, 1), ((8, 12, 16), 0, 2), ((16, 16, 16), 1, 3), ((12, 8, 8), 1, 4)]
-    cells, phis = [], []
+    cells = []
     for shape, prec, seed in cases:
         phi = cellgen.gaussian_levelset(shape, seed=seed)
-        phis.append(phi)
         with torch.cuda.stream(torch.cuda.Stream()):
-            cells.append(make_cell(phi, "phi", precision=prec))
+            cells.append(make_cell(phi, "phi", precision=prec, graphs=graphs))
+
+    def check(cs, cas, seeds):
+        for (shape, prec, _), seed, c in zip(cas, seeds, cs):
+            alone = make_cell(cellgen.gaussian_levelset(shape, seed=seed), "phi", precision=prec)
+            alone.solve()
+            for a, b in zip(c.homogenise(), alone.homogenise()):
+                assert np.array_equal(a, b)
+            alone.close()
+
     sts = solve_batch(cells)
     torch.cuda.synchronize()
     assert all(st["status"] == 0 for st in sts)
-    for (shape, prec, seed), phi, c in zip(cases, phis, cells):
-        alone = make_cell(phi, "phi", precision=prec)
-        alone.solve()
-        for a, b in zip(c.homogenise(), alone.homogenise()):
-            assert np.array_equal(a, b)
+    check(cells, cases, [c[2] for c in cases])
     _, ref = oracle_levelset((8, 8, 8), 1)
     assert max(block_errors(*cells[0].homogenise(), ref)) < 1e-8
+    # new designs in the same handles: the same batch (graph reused for graphs = 2)
+    seeds2 = [c[2] + 10 for c in cases]
+    for (shape, _, _), seed, c in zip(cases, seeds2, cells):
+        c.update(torch.as_tensor(cellgen.gaussian_levelset(shape, seed=seed), device=dev()))
+    sts = solve_batch(cells)
+    torch.cuda.synchronize()
+    assert all(st["status"] == 0 for st in sts)
+    check(cells, cases, seeds2)
+    # a handle of the cached batch destroyed: the rest solve as a new batch
+    cells[1].close()
+    rest = [cells[0], cells[2], cells[3]]
+    sts = solve_batch(rest)
+    torch.cuda.synchronize()
+    assert all(st["status"] == 0 for st in sts)
+    check(rest, [cases[0], cases[2], cases[3]], [seeds2[0], seeds2[2], seeds2[3]])
 
 
 @pytest.mark.parametrize("precision", [0, 1])
@@ -604,3 +627,32 @@ def test_autotuned_tiles_leave_the_solve_unchanged():
     assert all(t["xt"] == 0 and t["L"] == 0 for t in sa["tc_tiles"])
     for t in sb["tc_tiles"]:
         assert t["xt"] in (8, 16, 32) and 1 <= t["L"] <= 24 and t["us"] > 0
+
+
+def test_stencil_loads_per_thread_leave_the_solve_unchanged():
+    """The coarse levels' stencil apply computes every (node, load) with the
+    same operation sequence for 1, 3 or 9 loads per thread: solves with each
+    forced value equal the default one bitwise, and the set-up tuner reports
+    one of them for the levels above the four-lane size (level 1 of this
+    ragged 40 x 36 x 48 grid has 8640 nodes)."""
+    phi = cellgen.gaussian_levelset((40, 36, 48), seed=5)
+    tuned = make_cell(phi, "phi")
+    st = tuned.solve()
+    for blk in range(2):
+        assert st["stencil_rg"][blk][0] == 0
+        assert st["stencil_rg"][blk][1] in (1, 3, 9)
+    ref = tuned.homogenise()
+    for rg in (1, 3, 9):
+        c = make_cell(phi, "phi", autotune=0, graphs=0)
+        for blk in ("A", "Sbar"):
+            for lev in range(1, st["nlevels_u" if blk == "A" else "nlevels_phi"]):
+                c.set_stencil_rg(blk, lev, rg)
+        s = c.solve()
+        assert s["iters"] == st["iters"]
+        for x, y in zip(c.homogenise(), ref):
+            assert np.array_equal(x, y)
+        c.close()
+    with pytest.raises(Exception):
+        tuned.set_stencil_rg("A", 0, 3)
+    with pytest.raises(Exception):
+        tuned.set_stencil_rg("A", 1, 4)
