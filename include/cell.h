@@ -372,8 +372,8 @@ int cell_apply_block(cell_handle* h, int block, const void* x, void* y, int nrhs
  * xt = nodes along x per CTA (8, 16 or 32, at most nx rounded up to a multiple
  * of 8), L = z-planes per CTA chunk (>= 1; values above nz act as nz); xt = L
  * = 0 restores the default tile.  Results do not depend on the tile (each
- * node's tensor-core sequence and epilogue are the same); it changes launch
- * geometry and speed only.  Takes effect for later launches; a solve graph
+ * node's tensor-core sequence and epilogue arithmetic are the same); it
+ * changes launch geometry and speed only.  Takes effect for later launches; a solve graph
  * captured before the call keeps the tile it was captured with.  Errors:
  * CELL_EINVAL for a null handle, an unknown block, a tile outside those ranges,
  * or a handle without the tensor-core path (FP64 precision, tensor_cores = 0

@@ -34,8 +34,11 @@
 // A CTA owns XT x 16 nodes (XT = 8, 16 or 32; ragged edges masked) of one load
 // (elastic) or four loads (Schur) and a chunk of L z-planes.  It stages node
 // planes with 4-byte cp.async two planes ahead of use into a ring of six,
-// issues the MMAs of plane k (one thread) into one of two TMEM buffers, and
-// its eight warps run the epilogue of plane k - 1 meanwhile.
+// issues the MMAs of plane k (one thread per M tile) into one of two TMEM
+// buffers, and its eight warps run the epilogue of plane k - 1 meanwhile.
+// The epilogue's node-wise operands (residual, iterate, inverse diagonal) and
+// the 8 rho of each node are prefetched into registers one plane ahead, and
+// into L2 three planes ahead.
 //
 // Inputs enter the tensor core as TF32 (10 mantissa bits) and B is rounded to
 // TF32 on the host, so results carry TF32 rounding (about 1e-3 relative),
@@ -58,7 +61,7 @@ constexpr int kRing = kAhead + 4;       // staged planes (see the ring argument 
 constexpr int kPairs = 5;               // MMAs per plane and tile
 constexpr int kMmas = 3 * kPairs;
 constexpr int kBFloats = kMmas * 256;   // B: kMmas tiles of 32 x 8
-constexpr int kMinSmem = 80 * 1024;     // at most two CTAs per SM (TMEM: 2 x 256 columns)
+constexpr int kSmemPerSM = 228 * 1024;  // shared memory of an SM (1 KB of it reserved per CTA)
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 // Neighbour (dx, dy) of K half h of pair p; half 1 of pair 4 is a dummy (zero B).
@@ -94,10 +97,14 @@ NcGeom make_geom(int nx, int ny, int nz, int L, int XT) {
   g.off_b = kRing * g.PS;
   g.off_bar = g.off_b + kBFloats * 4;
   g.smem = g.off_bar + 64 + 8 * (kMmas + kPairs);
-  if (g.smem < kMinSmem) g.smem = kMinSmem;
   int c = 32;
   while (c < 2 * g.TX * 32) c <<= 1;
   g.tcols = c;
+  // no more CTAs resident per SM than TMEM holds (512 columns): pad the
+  // shared memory so that one more CTA would not fit
+  const int max_ctas = 512 / g.tcols;
+  const int min_smem = kSmemPerSM / (max_ctas + 1) + 1 - 1024;
+  if (g.smem < min_smem) g.smem = min_smem;
   return g;
 }
 
@@ -110,41 +117,53 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ int wrap(int v, int n) {
   v %= n;
   return v < 0 ? v + n : v;
 }
 
-// Node-wise output of one (node, load, component) with the semantics of the
-// SIMT kernels (ApplyMode); e0, e1, e2 are the prefetched operands of the mode.
+// Node-wise output of one (node, slot) with the semantics of the SIMT kernels
+// (ApplyMode); e0, e1, e2 are the prefetched operands of the mode.  y, sol and
+// dout point at the slot's plane of the outputs, n is the node (32-bit index).
 template <int MODE>
-__device__ __forceinline__ void node_out(const ApplyArgs<float>& a, int r, i64 o, float acc, float dold,
-                                         float e0, float e1, float e2, float c1, float c2) {
+__device__ __forceinline__ void node_out(const ApplyArgs<float>& a, float* y, float* sol, float* dout, int n,
+                                         float acc, float dold, float e0, float e1, float e2, float c1, float c2) {
+  // explicit roundings: the result must not depend on how the compiler
+  // contracts these expressions in the different kernel forms
   if (MODE == AM_LINEAR) {
-    float v = a.alpha * acc;
-    if (a.b) v += a.beta * e0;
-    a.y[r * a.ys + o] = v;
+    float v = __fmul_rn(a.alpha, acc);
+    if (a.b) v = fmaf(a.beta, e0, v);
+    y[n] = v;
   } else if (MODE == AM_CHEB || MODE == AM_CHEB_LAST) {
-    const float rr = e0 - acc;              // e0 = residual, e1 = iterate, e2 = dinv
-    a.y[r * a.ys + o] = rr;
-    a.sol[r * a.ss + o] = (a.sol_zero ? 0.f : e1) + dold;
-    if (MODE == AM_CHEB) a.dout[r * a.ds + o] = c1 * dold + c2 * e2 * rr;
+    const float rr = __fsub_rn(e0, acc);    // e0 = residual, e1 = iterate, e2 = dinv
+    y[n] = rr;
+    sol[n] = __fadd_rn(a.sol_zero ? 0.f : e1, dold);
+    if (MODE == AM_CHEB) dout[n] = fmaf(c1, dold, __fmul_rn(__fmul_rn(c2, e2), rr));
   } else {                                   // AM_RESID_CHEB0: e0 = b, e2 = dinv
-    const float rr = e0 - acc;
-    a.y[r * a.ys + o] = rr;
-    a.dout[r * a.ds + o] = c2 * e2 * rr;
+    const float rr = __fsub_rn(e0, acc);
+    y[n] = rr;
+    dout[n] = __fmul_rn(__fmul_rn(c2, e2), rr);
   }
 }
 
-template <int KIND, int MODE>
-__global__ void __launch_bounds__(kThreads, 2)
+// TPW = M tiles per warp in the epilogue: 2 for 32-node-wide CTA tiles (two
+// CTAs per SM), 1 for narrower ones (up to four CTAs per SM, fewer registers).
+template <int KIND, int MODE, int TPW>
+__global__ void __launch_bounds__(kThreads, TPW == 2 ? 2 : 3)
 k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, int nrhs, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   constexpr int UPL = KIND == NK_UU ? 1 : 4;   // loads per CTA
   constexpr int NS = KIND == NK_UU ? 3 : 4;    // record slots read and written
   const int tid = threadIdx.x, w = tid >> 5, l = tid & 31;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const i64 nxy = (i64)nx * ny, nn = nxy * nz;
+  // 32-bit node indices within a load: the launcher checks that 4 nn and four
+  // times every vector stride stay below 2^31; each load's 64-bit base is
+  // formed once
+  const int nxy = nx * ny, nn = nxy * nz;
   const int x0 = blockIdx.x * g.XT, y0 = blockIdx.y * kTY;
   const int zc = blockIdx.z % g.zchunks;
   const int r0 = (blockIdx.z / g.zchunks) * UPL;
@@ -232,13 +251,15 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   }
   auto stage_plane = [&](int p) {
     if (p > L + 1) return;
-    const i64 zoff = (i64)wrap(z0 - 1 + p, nz) * nxy;
+    int zs = z0 - 1 + p;
+    zs = zs < 0 ? zs + nz : (zs >= nz ? zs - nz : zs);
+    const int zoff = zs * nxy;
     const uint32_t dst0 = splanes + (uint32_t)((p % kRing) * g.PS);
 #pragma unroll
     for (int u = 0; u < kRecPerThread; ++u) {
       if (roff[u] < 0) continue;
       const uint32_t d = dst0 + (uint32_t)((tid + u * kThreads) * 16);
-      const i64 off = zoff + roff[u];
+      const int off = zoff + roff[u];
 #pragma unroll
       for (int s = 0; s < 4; ++s)
         if (in[s]) cp_async4(d + 4 * s, in[s] + off);
@@ -275,7 +296,34 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   const int xi = row & 7, yi = row >> 3;
   const int gy = y0 + yi;
   const int ym = gy == 0 ? ny - 1 : gy - 1;
-  constexpr int kTilesPerWarp = 2;   // TX <= 4 tiles, two warps per lane quarter
+  constexpr int kTilesPerWarp = TPW;   // TX <= 2 TPW tiles, two warps per lane quarter
+
+  // Output and operand planes of slot s: the CTA's first load has 64-bit
+  // bases; a slot adds a 32-bit offset (component plane for the elastic block,
+  // load for the Schur block).
+  float* const yB = a.y + (i64)r0 * a.ys;
+  float* const solB = a.sol ? a.sol + (i64)r0 * a.ss : nullptr;
+  float* const doutB = a.dout ? a.dout + (i64)r0 * a.ds : nullptr;
+  const float* const bB = a.b ? a.b + (i64)r0 * a.bs : nullptr;
+  auto soff = [&](int s, i64 stride) -> int { return KIND == NK_UU ? s * nn : s * (int)stride; };
+
+  // Per tile j of the thread: the node's in-plane index and those of its 8
+  // elements' (x, y) positions (o & 3 = ex + 2 ey), fixed for every plane.
+  int pin[kTilesPerWarp], rin[kTilesPerWarp][4];
+  bool valid[kTilesPerWarp];
+#pragma unroll
+  for (int j = 0; j < kTilesPerWarp; ++j) {
+    const int t = (w >> 2) + 2 * j;
+    const int gxn = x0 + 8 * t + xi;
+    valid[j] = t < g.TX && gxn < nx && gy < ny;
+    const int xm = gxn == 0 ? nx - 1 : gxn - 1;
+    pin[j] = gy * nx + gxn;
+    rin[j][0] = ym * nx + xm;
+    rin[j][1] = ym * nx + gxn;
+    rin[j][2] = gy * nx + xm;
+    rin[j][3] = gy * nx + gxn;
+  }
+
 
   // Epilogue of output plane k in two parts.  prefetch(k) loads the node-wise
   // operands and the 8 rho values of each of the thread's nodes into registers
@@ -285,46 +333,56 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
   // sum -> output.
   float rho[kTilesPerWarp][8];
   float e0[kTilesPerWarp][NS], e1[kTilesPerWarp][NS], e2[kTilesPerWarp][NS];
-  bool valid[kTilesPerWarp];
   auto prefetch = [&](int k) {
     const int gz = z0 + k;
-    const int zm = gz == 0 ? nz - 1 : gz - 1;
+    const int zo = gz * nxy, zmo = (gz == 0 ? nz - 1 : gz - 1) * nxy;
 #pragma unroll
     for (int j = 0; j < kTilesPerWarp; ++j) {
-      const int t = (w >> 2) + 2 * j;
-      const int gxn = x0 + 8 * t + xi;
-      valid[j] = t < g.TX && gxn < nx && gy < ny;
       if (!valid[j]) continue;
-      const int xm = gxn == 0 ? nx - 1 : gxn - 1;
 #pragma unroll
-      for (int o = 0; o < 8; ++o) {
-        const int ix = (o & 1) ? gxn : xm, iy = ((o >> 1) & 1) ? gy : ym, iz = (o >> 2) ? gz : zm;
-        rho[j][o] = __ldg(a.rho + (i64)iz * nxy + (i64)iy * nx + ix);
-      }
-      const i64 n = (i64)gz * nxy + (i64)gy * nx + gxn;
+      for (int o = 0; o < 8; ++o) rho[j][o] = __ldg(a.rho + ((o >> 2) ? zo : zmo) + rin[j][o & 3]);
+      const int n = zo + pin[j];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         e0[j][s] = e1[j][s] = e2[j][s] = 0.f;
         if (KIND == NK_SS4 && !on[s]) continue;
-        const int r = KIND == NK_UU ? r0 : r0 + s;
-        const i64 o = KIND == NK_UU ? (i64)s * nn + n : n;
+        const int nd = (KIND == NK_UU ? s * nn : 0) + n;   // inverse diagonal [NC][nn]
         if (MODE == AM_LINEAR) {
-          if (a.b) e0[j][s] = a.b[r * a.bs + o];
+          if (bB) e0[j][s] = bB[soff(s, a.bs) + n];
         } else if (MODE == AM_CHEB || MODE == AM_CHEB_LAST) {
-          e0[j][s] = a.y[r * a.ys + o];
-          if (!a.sol_zero) e1[j][s] = a.sol[r * a.ss + o];
-          if (MODE == AM_CHEB) e2[j][s] = __ldg(a.dinv + o);
+          e0[j][s] = yB[soff(s, a.ys) + n];
+          if (!a.sol_zero) e1[j][s] = solB[soff(s, a.ss) + n];
+          if (MODE == AM_CHEB) e2[j][s] = __ldg(a.dinv + nd);
         } else {
-          e0[j][s] = a.b[r * a.bs + o];
-          e2[j][s] = __ldg(a.dinv + o);
+          e0[j][s] = bB[soff(s, a.bs) + n];
+          e2[j][s] = __ldg(a.dinv + nd);
         }
+      }
+    }
+  };
+  // L2 prefetch of the node-wise operands of output plane k (two steps before
+  // prefetch(k) loads them into registers, so that those loads hit L2)
+  auto l2_prefetch = [&](int k) {
+    if (k >= L) return;
+    const int zo = (z0 + k) * nxy;
+#pragma unroll
+    for (int j = 0; j < kTilesPerWarp; ++j) {
+      if (!valid[j]) continue;
+      const int n = zo + pin[j];
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        if (KIND == NK_SS4 && !on[s]) continue;
+        const float* p0 = MODE == AM_LINEAR || MODE == AM_RESID_CHEB0 ? bB + soff(s, a.bs) : yB + soff(s, a.ys);
+        if (MODE != AM_LINEAR || bB) prefetch_l2(p0 + n);
+        if ((MODE == AM_CHEB || MODE == AM_CHEB_LAST) && !a.sol_zero) prefetch_l2(solB + soff(s, a.ss) + n);
+        if (MODE == AM_CHEB || MODE == AM_RESID_CHEB0) prefetch_l2(a.dinv + (KIND == NK_UU ? s * nn : 0) + n);
       }
     }
   };
   auto finish = [&](int k) -> bool {
     if (!tc::mbar_wait_bounded(bar + (k & 1), (uint32_t)((k >> 1) & 1), kWaitLimit)) return false;
     tc::fence_after_sync();
-    const int gz = z0 + k;
+    const int zo = (z0 + k) * nxy;
     const unsigned char* pl = planes + ((k + 1) % kRing) * g.PS;   // the output plane's records
 #pragma unroll
     for (int j = 0; j < kTilesPerWarp; ++j) {
@@ -335,17 +393,16 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
       if (!valid[j]) continue;
       const float4 rec = *reinterpret_cast<const float4*>(pl + ((yi + 1) * RW + 8 * t + xi + 1) * 16);
       const float dold[4] = {rec.x, rec.y, rec.z, rec.w};
-      const int gxn = x0 + 8 * t + xi;
-      const i64 n = (i64)gz * nxy + (i64)gy * nx + gxn;
+      const int n = zo + pin[j];
 #pragma unroll
       for (int s = 0; s < NS; ++s) {
         if (KIND == NK_SS4 && !on[s]) continue;
         float acc = 0.f;
 #pragma unroll
         for (int o = 0; o < 8; ++o) acc = fmaf(rho[j][o], T[4 * o + s], acc);
-        const int r = KIND == NK_UU ? r0 : r0 + s;
-        const i64 o = KIND == NK_UU ? (i64)s * nn + n : n;
-        node_out<MODE>(a, r, o, acc, dold[s], e0[j][s], e1[j][s], e2[j][s], c1, c2);
+        node_out<MODE>(a, yB + soff(s, a.ys), solB ? solB + soff(s, a.ss) : nullptr,
+                       doutB ? doutB + soff(s, a.ds) : nullptr, n, acc, dold[s], e0[j][s], e1[j][s],
+                       e2[j][s], c1, c2);
       }
     }
     return true;
@@ -366,6 +423,8 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
     stage_plane(p);
     cp_async_commit();
   }
+  l2_prefetch(0);
+  l2_prefetch(1);
   bool aborted = false;
   int issued = 0, waited = 0;
   for (int k = 0; k < L; ++k) {
@@ -382,6 +441,7 @@ k_nc(const ApplyArgs<float> a, const float* __restrict__ Btab, const NcGeom g, i
       else aborted = true;
     }
     prefetch(k);
+    l2_prefetch(k + 2);
   }
   if (!aborted) {
     if (finish(L - 1)) ++waited;
@@ -457,14 +517,24 @@ bool launch(const ApplyArgs<float>& a, const float* Btab, int nrhs, int* err, cu
   const int units = units_of(KIND, nrhs);
   const NcGeom g = geom_for(KIND, a, nrhs, tile);
   if ((long long)g.zchunks * units > 65535 || g.gy > 65535) return false;
+  // 32-bit node indices and slot offsets inside the kernel
+  const long long nn = (long long)a.nx * a.ny * a.nz;
+  const long long lim = 1ll << 31;
+  if (4 * nn >= lim || 4 * a.xs >= lim || 4 * a.ys >= lim || 4 * a.ss >= lim || 4 * a.ds >= lim ||
+      4 * a.bs >= lim)
+    return false;
   const dim3 grid((unsigned)g.gx, (unsigned)g.gy, (unsigned)(g.zchunks * units));
-  note_launch(), k_nc<KIND, MODE><<<grid, kThreads, g.smem, s>>>(a, Btab, g, nrhs, err);
+  if (g.TX > 2)
+    note_launch(), k_nc<KIND, MODE, 2><<<grid, kThreads, g.smem, s>>>(a, Btab, g, nrhs, err);
+  else
+    note_launch(), k_nc<KIND, MODE, 1><<<grid, kThreads, g.smem, s>>>(a, Btab, g, nrhs, err);
   return true;
 }
 
 template <int KIND, int MODE>
 void set_attr(int smem) {
-  cudaFuncSetAttribute(k_nc<KIND, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_nc<KIND, MODE, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaFuncSetAttribute(k_nc<KIND, MODE, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
 }  // namespace
@@ -542,12 +612,13 @@ bool apply_nc(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, 
 }
 
 // Tile autotuner.  Every (XT, L) candidate computes bitwise the same result
-// (a node's MMA sequence and epilogue do not depend on the tiling), so the
-// choice is free: each candidate is timed on the caller's buffers in the given
-// mode (one warm-up launch, then kTuneReps launches between CUDA events on the
-// stream) and the fastest kept.  Candidates: XT in {8, 16, 32} up to the grid's
-// widest tile, L in {4, 8, ..., 256} up to nz (and nz itself), within the
-// launch limits.  Returns the default tile if nothing could be timed.
+// (a node's MMA sequence and epilogue arithmetic do not depend on the tiling),
+// so the choice is free: each candidate is timed on the caller's buffers in
+// the given mode (one warm-up launch, then kTuneReps launches between CUDA
+// events on the stream) and the fastest kept.  Candidates: XT in {8, 16, 32}
+// up to the grid's widest tile, L in {4, 8, ..., 256} up to nz (and nz
+// itself), within the launch limits.  Returns the default tile if nothing
+// could be timed.
 NcTile nc_autotune(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
                    cudaStream_t s, float* best_us) {
   constexpr int kTuneReps = 3;

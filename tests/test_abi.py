@@ -42,16 +42,22 @@ def test_exports_every_declared_symbol(B):
 
 
 def test_struct_layout_matches_c(B, tmp_path):
+    """Size and every field offset of the ABI structs agree between the C
+    header and the ctypes mirrors (a field out of order fails here)."""
+    structs = (("cell_options", B.cell_options), ("cell_desc", B.cell_desc), ("cell_stats", B.cell_stats))
+    lines, want = [], []
+    for cname, py in structs:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        want.append(ctypes.sizeof(py))
+        for fname, _ in py._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {fname}));')
+            want.append(getattr(py, fname).offset)
     src = tmp_path / "sz.c"
     src.write_text('#include "cell.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(cell_options), '
-                   'sizeof(cell_desc), sizeof(cell_stats), offsetof(cell_desc, opt), '
-                   'offsetof(cell_desc, stream)); return 0;}\n')
+                   'int main(void){' + "".join(lines) + ' return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    want = [ctypes.sizeof(B.cell_options), ctypes.sizeof(B.cell_desc), ctypes.sizeof(B.cell_stats),
-            B.cell_desc.opt.offset, B.cell_desc.stream.offset]
     assert [int(v) for v in out] == want
 
 

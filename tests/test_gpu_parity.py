@@ -656,3 +656,26 @@ def test_stencil_loads_per_thread_leave_the_solve_unchanged():
         tuned.set_stencil_rg("A", 0, 3)
     with pytest.raises(Exception):
         tuned.set_stencil_rg("A", 1, 4)
+
+
+@pytest.mark.parametrize("shape", [(24, 20, 32), (17, 16, 12)])
+def test_smoother_tiles_leave_the_solve_unchanged(shape):
+    """Every mode of the tensor-core smoothers in the V-cycle (Chebyshev steps
+    with and without a zero start, last step, residual with the first step)
+    gives the same bits for every CTA tile, one or two M tiles per warp: forced
+    tiles give the solve bitwise, on grids whose x tiles, 16-row y tiles and z
+    chunks are ragged (nz x ny x nx given)."""
+    phi = cellgen.gaussian_levelset(shape, seed=8)
+    outs = []
+    for xt, L in ((16, 5), (8, 3), (32 if shape[2] >= 32 else 16, 64)):
+        c = make_cell(phi, "phi", autotune=0, graphs=0)
+        for blk in ("A", "Sbar"):
+            c.set_tile(blk, xt, L)
+        st = c.solve()
+        assert st["tc_tiles"][0]["xt"] == xt
+        outs.append((st["iters"], c.homogenise()))
+        c.close()
+    for i, (its, H) in enumerate(outs[1:]):
+        assert its == outs[0][0]
+        for x, y in zip(H, outs[0][1]):
+            assert np.array_equal(x, y), (i, np.abs(x - y).max() / np.abs(y).max())
