@@ -38,7 +38,7 @@
 // buffers, and its eight warps run the epilogue of plane k - 1 meanwhile.
 // The epilogue's node-wise operands (residual, iterate, inverse diagonal) and
 // the 8 rho of each node are prefetched into registers one plane ahead, and
-// into L2 three planes ahead.
+// into L2 two steps before that.
 //
 // Inputs enter the tensor core as TF32 (10 mantissa bits) and B is rounded to
 // TF32 on the host, so results carry TF32 rounding (about 1e-3 relative),
@@ -133,7 +133,8 @@ template <int MODE>
 __device__ __forceinline__ void node_out(const ApplyArgs<float>& a, float* y, float* sol, float* dout, int n,
                                          float acc, float dold, float e0, float e1, float e2, float c1, float c2) {
   // explicit roundings: the result must not depend on how the compiler
-  // contracts these expressions in the different kernel forms
+  // contracts these expressions in each instantiation (tiles per warp, modes),
+  // so that every CTA tile gives the same bits
   if (MODE == AM_LINEAR) {
     float v = __fmul_rn(a.alpha, acc);
     if (a.b) v = fmaf(a.beta, e0, v);
