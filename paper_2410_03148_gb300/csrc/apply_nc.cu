@@ -616,10 +616,10 @@ bool apply_nc(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, 
 // (a node's MMA sequence and epilogue arithmetic do not depend on the tiling),
 // so the choice is free: each candidate is timed on the caller's buffers in
 // the given mode (one warm-up launch, then kTuneReps launches between CUDA
-// events on the stream) and the fastest kept.  Candidates: XT in {8, 16, 32}
-// up to the grid's widest tile, L in {4, 8, ..., 256} up to nz (and nz
-// itself), within the launch limits.  Returns the default tile if nothing
-// could be timed.
+// events on the stream, in two rounds of opposite order, the better round
+// kept) and the fastest kept.  Candidates: XT in {8, 16, 32} up to the grid's
+// widest tile, L in {4, 8, ..., 256} up to nz (and nz itself), within the
+// launch limits.  Returns the default tile if nothing could be timed.
 NcTile nc_autotune(int kind, const ApplyArgs<float>& a, const float* Btab, int mode, int nrhs, int* err,
                    cudaStream_t s, float* best_us) {
   constexpr int kTuneReps = 3;
@@ -633,12 +633,27 @@ NcTile nc_autotune(int kind, const ApplyArgs<float>& a, const float* Btab, int m
   }
   const int xts[] = {8, 16, 32};
   const int Ls[] = {4, 8, 16, 32, 64, 128, 256};
+  NcTile cand[24];
+  int nc = 0;
   for (int xt : xts) {
     if (xt > max_xt(a.nx)) break;
     for (int i = 0; i <= 7; ++i) {
       int L = i < 7 ? Ls[i] : a.nz;
       if (i < 7 && L >= a.nz) continue;   // nz itself is the last candidate
-      const NcTile t{xt, L};
+      cand[nc++] = NcTile{xt, L};
+    }
+  }
+  // the GPU warms up (clocks, caches) over the first launches: a few launches
+  // of the default tile first, then two rounds over the candidates in opposite
+  // orders, each candidate keeping its faster round, so that no candidate is
+  // favoured by its place in the sequence
+  for (int r = 0; r < 2 * kTuneReps; ++r) apply_nc(kind, a, Btab, mode, nrhs, err, s, NcTile{0, 0});
+  float tbest[24];
+  for (int c = 0; c < nc; ++c) tbest[c] = 3.0e38f;
+  for (int round = 0; round < 2; ++round)
+    for (int ci = 0; ci < nc; ++ci) {
+      const int c = round == 0 ? ci : nc - 1 - ci;
+      const NcTile t = cand[c];
       if (!apply_nc(kind, a, Btab, mode, nrhs, err, s, t)) continue;
       cudaEventRecord(e0, s);
       bool ok = true;
@@ -647,12 +662,13 @@ NcTile nc_autotune(int kind, const ApplyArgs<float>& a, const float* Btab, int m
       float ms = 0.f;
       if (!ok || cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
         continue;
-      if (ms < best_t) {
-        best_t = ms;
-        best = t;
-      }
+      if (ms < tbest[c]) tbest[c] = ms;
     }
-  }
+  for (int c = 0; c < nc; ++c)
+    if (tbest[c] < best_t) {
+      best_t = tbest[c];
+      best = cand[c];
+    }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (best_us) *best_us = best.xt ? best_t * 1000.f / kTuneReps : 0.f;
